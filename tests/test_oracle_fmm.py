@@ -1,0 +1,137 @@
+"""Pins of the oracle's step-by-step FMM against exact special cases, brute
+force and invariants (no GPU)."""
+import numpy as np
+import pytest
+
+from oracle import fmm, green, pm
+from paper_2011_07099_gb300 import inputs
+
+
+def _pm_s1(rho):
+    n = rho.shape[0]
+    return pm.pm(pm.masses(rho), green.g_s1, green.grad_g_s1, green.self_term(n))
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("n", [8, 16])
+def test_two_level_tree_with_gridlet_equal_subgrid_is_exact(n):
+    # Sec. 3: with 2 levels and gridlet == sub-grid, FMM and PM coincide.
+    rho = inputs.plummer(n, n_clumps=4, seed=n, a_min=0.5, a_max=2.0)
+    S = n // 4
+    phi, g = fmm.solve(rho, 2, S)
+    p_ref, g_ref = pm.direct(pm.masses(rho), green.g_s1, green.grad_g_s1, green.self_term(n))
+    assert _rel(phi, p_ref) < 1e-12
+    assert _rel(g, g_ref) < 1e-12
+
+
+def test_p2m_identity_when_gridlet_is_subgrid_and_monopole_when_p_is_1():
+    np.testing.assert_allclose(fmm.p2m_matrix(4, 4), np.eye(64), atol=1e-12)
+    np.testing.assert_allclose(fmm.p2m_matrix(4, 1), np.ones((1, 64)), atol=1e-13)
+
+
+def test_p2m_two_points_per_dimension_closed_form():
+    # 1-D check: two gridlet points at -1/4, +1/4 of the node carry mass and
+    # dipole, M_pm = Q0/2 +- 2 Q1 for a cell at offset x with unit mass.
+    S, p = 4, 2
+    P = fmm.p2m_matrix(S, p)
+    # cell (cx, 0, 0) at x = (cx + 1/2)/S - 1/2; gridlet s = (sx, 0, 0)
+    for cx in range(S):
+        x = (cx + 0.5) / S - 0.5
+        y = z = (0.5) / S - 0.5
+        col = P[:, cx]                     # cell (0,0,cx)
+        wy = [0.5 - 2 * y, 0.5 + 2 * y]
+        wz = [0.5 - 2 * z, 0.5 + 2 * z]
+        wx = [0.5 - 2 * x, 0.5 + 2 * x]
+        exp = np.array([wz[a] * wy[b] * wx[c] for a in range(2) for b in range(2) for c in range(2)])
+        np.testing.assert_allclose(col, exp, atol=1e-13)
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_m2m_after_p2m_equals_p2m_to_the_parent(p):
+    rho = inputs.lognormal(16, sigma=1.0, seed=7)
+    m = pm.masses(rho)
+    M3 = fmm.p2m(m, 3, p)
+    np.testing.assert_allclose(fmm.m2m(M3, p), fmm.p2m(m, 2, p), atol=1e-14 * np.abs(M3).max())
+
+
+def test_interaction_zone_sizes_and_translation_invariance():
+    assert len(fmm.interaction_list(2, (0, 0, 0))) == 37
+    for lev in (3, 4):
+        n = 2 ** lev
+        for node in [(0, 0, 0), (1, 2, 3), (n - 1, n - 2, 0), (5 % n, 7 % n, 6 % n)]:
+            il = fmm.interaction_list(lev, node)
+            assert len(il) == 189
+            c = tuple(i % 2 for i in node)
+            offs = fmm.interaction_offsets(lev, c)
+            want = {tuple((np.array(node) - np.array(o)) % n) for o in offs}
+            assert want == il
+
+
+@pytest.mark.parametrize("L", [3, 4])
+def test_zones_cover_every_leaf_exactly_once(L):
+    leaf = (1, 2, 3) if L == 3 else (5, 0, 15)
+    count = {}
+    for lev in range(2, L + 1):
+        anc = tuple(i >> (L - lev) for i in leaf)
+        for src in fmm.interaction_list(lev, anc):
+            sh = L - lev
+            for a in range(2 ** sh):
+                for b in range(2 ** sh):
+                    for c in range(2 ** sh):
+                        k = ((src[0] << sh) + a, (src[1] << sh) + b, (src[2] << sh) + c)
+                        count[k] = count.get(k, 0) + 1
+    for nb in fmm.neighbours(L, leaf):
+        count[nb] = count.get(nb, 0) + 1
+    assert len(count) == 8 ** L and set(count.values()) == {1}
+
+
+def test_error_against_pm_falls_with_order_and_net_force_vanishes():
+    rho = inputs.lognormal(32, sigma=0.5, seed=11)
+    ref_phi, ref_g = _pm_s1(rho)
+    errs = []
+    for p in (2, 3, 4):
+        phi, g = fmm.solve(rho, 3, p)
+        errs.append((_rel(phi, ref_phi), _rel(g, ref_g)))
+        m = pm.masses(rho)
+        f = (m[None] * g).sum(axis=(1, 2, 3))
+        assert np.abs(f).max() < 1e-11 * (np.abs(m)[None] * np.abs(g)).sum()
+    assert errs[0][0] > errs[1][0] > errs[2][0]
+    assert errs[0][1] > errs[1][1] > errs[2][1]
+    assert errs[2][1] < 2e-3
+
+
+def test_solve_at_matches_full_solve():
+    rho = inputs.plummer(32, n_clumps=8, seed=3)
+    L, p = 3, 2
+    phi, g = fmm.solve(rho, L, p)
+    full = np.concatenate([phi[None], g])
+    leaves = np.array([[0, 0, 0], [7, 3, 1], [2, 7, 7]])
+    got = fmm.solve_at(rho, L, p, leaves)
+    S = 32 // 2 ** L
+    for i, (a, b, c) in enumerate(leaves):
+        ref = full[:, a * S:(a + 1) * S, b * S:(b + 1) * S, c * S:(c + 1) * S].reshape(4, -1)
+        np.testing.assert_allclose(got[i], ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+def test_planted_mistake_in_l2l_is_caught(monkeypatch):
+    # Using T instead of its transpose in eq. fmm3 breaks the exact-parent
+    # property that the convergence pins rely on.
+    rho = inputs.lognormal(16, sigma=0.5, seed=2)
+    ref_phi, ref_g = _pm_s1(rho)
+    good = _rel(fmm.solve(rho, 3, 2)[1], ref_g)
+    monkeypatch.setattr(fmm, "l2l", lambda F, p, c: F @ fmm.m2m_matrix(p, c).T)
+    bad = _rel(fmm.solve(rho, 3, 2)[1], ref_g)
+    assert bad > 3 * good
+
+
+def test_planted_sign_mistake_in_m2l_is_caught(monkeypatch):
+    n = 8
+    rho = inputs.plummer(n, n_clumps=2, seed=4, a_min=0.5, a_max=1.0)
+    orig = fmm.m2l_kernel
+    monkeypatch.setattr(fmm, "m2l_kernel", lambda lev, p, off: orig(lev, p, tuple(-o for o in off)))
+    phi, g = fmm.solve(rho, 2, 2)
+    p_ref, g_ref = pm.direct(pm.masses(rho), green.g_s1, green.grad_g_s1, green.self_term(n))
+    assert _rel(g, g_ref) > 1e-3
