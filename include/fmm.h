@@ -1,0 +1,148 @@
+/*
+ * libfmm — natively periodic Fast Multipole Method on one GB300 (sm_103a).
+ *
+ * The method is Gnedin, "Natively Periodic Fast Multipole Method:
+ * Approximating the Optimal Green's Function" (arXiv:2011.07099).  A density
+ * field on a periodic N^3 mesh over the unit box is solved for the potential
+ * Phi (lap Phi = rho - mean rho, Sec. 1: G_0 = -1/(4 pi r)) and the
+ * acceleration g = -grad Phi, by an FMM whose interaction-zone Green's
+ * function is the approximately optimal periodic G_S1 of eq. gfs1 (Sec. 4):
+ *
+ *   G_S1(x) = -1/(4 pi |xhat|),  xhat_i = (9/(8 pi)) sin(pi x_i) - (1/(24 pi)) sin(3 pi x_i).
+ *
+ * Conventions shared by every entry point
+ *   - Mesh arrays are float32, C order [z][y][x] (x fastest), N^3 elements.
+ *     Cell (i,j,k) has its centre at ((i+1/2)/N, (j+1/2)/N, (k+1/2)/N).
+ *   - accel is structure-of-arrays: ax[N^3] | ay[N^3] | az[N^3].
+ *   - Device pointers must be 16-byte aligned device memory owned by the
+ *     caller; the library never frees them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  fmm_solve only enqueues work; it does not synchronise.
+ *   - Every int-returning call returns FMM_OK (0) or an FMM_ERR_* code; the
+ *     same code is kept per host thread and readable by fmm_last_error().
+ *   - A plan is not thread-safe: one host thread and one stream at a time.
+ *
+ * Tree (Sec. 2): level l has 2^l nodes per dimension; L is the leaf level,
+ * each leaf holds S^3 cells, S = N / 2^L.  Each node carries a gridlet of
+ * order^3 effective masses (order = N_g of the paper) on a cell-centred
+ * uniform mini-mesh.
+ */
+#ifndef FMM_H
+#define FMM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_plan fmm_plan;
+
+/* ---- error codes ---------------------------------------------------- */
+#define FMM_OK              0
+#define FMM_ERR_ARG         1   /* invalid argument (sizes, pointers, alignment, mode) */
+#define FMM_ERR_CUDA        2   /* a CUDA runtime call failed */
+#define FMM_ERR_TIMEOUT     3   /* a bounded device-side wait gave up */
+#define FMM_ERR_INTERNAL    4   /* a device-side consistency check failed */
+#define FMM_ERR_ALLOC       5   /* device or host allocation failed */
+#define FMM_ERR_UNSUPPORTED 6   /* valid request this build does not implement */
+
+/* ---- M2L precision modes (fmm_plan_set_precision) -------------------- */
+#define FMM_PREC_FP32    0  /* plain form: every stage FP32 on CUDA cores      */
+#define FMM_PREC_BF16    1  /* M2L levels >= 4 on tcgen05 tensor cores, BF16
+                               operands, FP32 accumulation in TMEM            */
+#define FMM_PREC_BF16X3  2  /* as BF16 with split products hi*hi+hi*lo+lo*hi */
+
+/* ---- plan lifecycle -------------------------------------------------- */
+
+/* Create a plan for an N^3 periodic mesh, leaf level L and gridlet order.
+ *   N     mesh cells per dimension; N = S * 2^L with S in {1, 2, 4, 8}.
+ *   L     leaf level, 2 <= L <= 8 (L = 2 is the two-level special case of
+ *         Sec. 3, exact when order == S; the general case is L >= 3, Sec. 2).
+ *   order gridlet points per dimension (N_g), 1 <= order <= 8.
+ * Allocates the plan's device buffers on the current device and tabulates
+ * G_S1 and grad G_S1 in FP64 for every level (Sec. 3 eq. fmm2, Sec. 4
+ * eq. gfs1).  Synchronises the device before returning.
+ * Returns NULL on error (fmm_last_error() gives the code). */
+fmm_plan* fmm_plan_create(int N, int L, int order);
+
+/* Release every resource of the plan (NULL is allowed).  Synchronises the
+ * device first so that no enqueued solve still uses the plan's buffers. */
+void fmm_plan_destroy(fmm_plan* plan);
+
+/* ---- solve ------------------------------------------------------------ */
+
+/* One full solve, enqueued on `stream`:
+ *   density   device, N^3 float32, read only.
+ *   potential device, N^3 float32, written (every element).
+ *   accel     device, 3*N^3 float32 SoA, written (every element).
+ * Steps (Sec. 2, Sec. 3 eqs. fmm1-fmm3): mean removal and P2M at the leaves,
+ * M2M up to level 2, M2L over the interaction zone at every level 2..L
+ * (37 periodic nodes at level 2, 189 below) with G_S1, L2L down the tree,
+ * and at each leaf L2P plus the direct near-zone sum over its 27 periodic
+ * neighbour leaves.  Buffers must not overlap.  Returns FMM_ERR_ARG for NULL
+ * or misaligned pointers, FMM_ERR_CUDA if a launch fails. */
+int fmm_solve(fmm_plan* plan, const float* density, float* potential,
+              float* accel, void* stream);
+
+/* End-to-end variant with HOST buffers (same shapes as fmm_solve).  Copies
+ * density host->device, solves, copies potential and accel device->host on
+ * `stream`, and synchronises the stream before returning.  The host buffers
+ * should be page-locked for full copy bandwidth; pageable memory works but is
+ * slower.  Device staging buffers are owned by the plan (allocated on first
+ * use). */
+int fmm_solve_host(fmm_plan* plan, const float* density_host,
+                   float* potential_host, float* accel_host, void* stream);
+
+/* ---- configuration ------------------------------------------------------ */
+
+/* Select the M2L arithmetic (FMM_PREC_*).  Takes effect at the next solve. */
+int fmm_plan_set_precision(fmm_plan* plan, int mode);
+
+/* Query plan parameters: writes N, L, order, S (any pointer may be NULL). */
+int fmm_plan_get_shape(const fmm_plan* plan, int* N, int* L, int* order, int* S);
+
+/* ---- per-stage timing --------------------------------------------------- */
+
+#define FMM_TIME_MEAN   0   /* a0 mean density                                   */
+#define FMM_TIME_P2M    1   /* a3 leaf gridlet masses                             */
+#define FMM_TIME_M2M    2   /* a4 all M2M levels                                  */
+#define FMM_TIME_M2L    3   /* a5/a6 all M2L levels                               */
+#define FMM_TIME_L2L    4   /* a7 all L2L levels                                  */
+#define FMM_TIME_P2P    5   /* a8+a9 fused L2P and near-zone sum                  */
+#define FMM_TIME_M2L_LEVEL0 6  /* slot 6 + l: M2L of level l alone (l = 2..8)     */
+#define FMM_TIME_SLOTS  16
+
+/* Enable (1) or disable (0) CUDA-event timing of every stage of later solves.
+ * Events are recorded on the solve's stream, so they bracket exactly the
+ * kernels of each stage.  Plan-owned events; no effect on results. */
+int fmm_plan_set_timing(fmm_plan* plan, int enable);
+
+/* Stage durations of the most recent timed solve in milliseconds, indexed by
+ * FMM_TIME_*; writes min(n, FMM_TIME_SLOTS) floats (unused slots 0).  Waits for
+ * that solve to finish.  FMM_ERR_ARG if timing was never enabled. */
+int fmm_plan_stage_times(fmm_plan* plan, float* ms, int n);
+
+/* ---- errors --------------------------------------------------------- */
+int fmm_last_error(void);
+const char* fmm_error_string(int code);
+
+/* ---- stage access (tests and diagnostics) ----------------------------- */
+
+#define FMM_STAGE_MULTIPOLE 0   /* gridlet masses of `level`: 8^level x order^3  */
+#define FMM_STAGE_LOCAL     1   /* local field of `level` after M2L and L2L:
+                                   8^level x 4 x order^3 (Phi, gx, gy, gz)      */
+#define FMM_STAGE_MEAN      2   /* mean density, 1 value (converted to float)    */
+
+/* Copy an internal stage buffer of the last solve into `dst` (device memory,
+ * `count` floats).  Node order is Morton: key = interleave(x, y, z) bits with
+ * x in the lowest bit.  Per node, values are [field][sz][sy][sx].  Enqueued on
+ * `stream`.  FMM_ERR_ARG if `count` is smaller than the stage. */
+int fmm_plan_copy_stage(fmm_plan* plan, int stage, int level, float* dst,
+                        size_t count, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM_H */

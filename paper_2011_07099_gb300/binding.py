@@ -1,0 +1,178 @@
+"""Thin ctypes binding of libfmm (include/fmm.h).  Argument marshalling only.
+
+The functions carry the C names.  Tensors are torch CUDA tensors (torch is
+used for device memory and streams only); the stream defaults to torch's
+current stream on the tensors' device.  The library must have been built
+(``paper_2011_07099_gb300.build.build()``); there is no fallback path: if the
+shared library is missing, loading raises.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfmm.so")
+
+FMM_OK = 0
+FMM_ERR_ARG = 1
+FMM_ERR_CUDA = 2
+FMM_ERR_TIMEOUT = 3
+FMM_ERR_INTERNAL = 4
+FMM_ERR_ALLOC = 5
+FMM_ERR_UNSUPPORTED = 6
+
+FMM_PREC_FP32 = 0
+FMM_PREC_BF16 = 1
+FMM_PREC_BF16X3 = 2
+
+FMM_STAGE_MULTIPOLE = 0
+FMM_STAGE_LOCAL = 1
+FMM_STAGE_MEAN = 2
+
+# every symbol include/fmm.h declares, with (restype, argtypes)
+_VP, _FP, _I, _SZ = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+SIGNATURES = {
+    "fmm_plan_create": (_VP, [_I, _I, _I]),
+    "fmm_plan_destroy": (None, [_VP]),
+    "fmm_solve": (_I, [_VP, _FP, _FP, _FP, _VP]),
+    "fmm_solve_host": (_I, [_VP, _FP, _FP, _FP, _VP]),
+    "fmm_plan_set_precision": (_I, [_VP, _I]),
+    "fmm_plan_get_shape": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                ctypes.POINTER(_I)]),
+    "fmm_last_error": (_I, []),
+    "fmm_error_string": (ctypes.c_char_p, [_I]),
+    "fmm_plan_copy_stage": (_I, [_VP, _I, _I, _FP, _SZ, _VP]),
+    "fmm_plan_set_timing": (_I, [_VP, _I]),
+    "fmm_plan_stage_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), _I]),
+}
+
+FMM_TIME_MEAN, FMM_TIME_P2M, FMM_TIME_M2M, FMM_TIME_M2L, FMM_TIME_L2L, FMM_TIME_P2P = range(6)
+FMM_TIME_M2L_LEVEL0 = 6
+FMM_TIME_SLOTS = 16
+
+_lib = None
+
+
+class FMMError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {lib().fmm_error_string(code).decode()} (code {code})")
+
+
+def lib():
+    """Load libfmm once.  Raises OSError if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"libfmm is not built ({LIB_PATH} missing); run paper_2011_07099_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc, where):
+    if rc != FMM_OK:
+        raise FMMError(rc, where)
+
+
+def _stream_of(t, stream):
+    if stream is not None:
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    import torch
+    return torch.cuda.current_stream(t.device).cuda_stream
+
+
+def fmm_plan_create(N, L, order):
+    h = lib().fmm_plan_create(int(N), int(L), int(order))
+    if not h:
+        raise FMMError(lib().fmm_last_error(), "fmm_plan_create")
+    return h
+
+
+def fmm_plan_destroy(plan):
+    lib().fmm_plan_destroy(plan)
+
+
+def fmm_solve(plan, density, potential, accel, stream=None):
+    _check(lib().fmm_solve(plan, density.data_ptr(), potential.data_ptr(), accel.data_ptr(),
+                           _stream_of(density, stream)), "fmm_solve")
+
+
+def fmm_solve_host(plan, density, potential, accel, stream=None):
+    """Host tensors (ideally pinned).  Synchronises ``stream`` before returning."""
+    s = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().fmm_solve_host(plan, density.data_ptr(), potential.data_ptr(), accel.data_ptr(), s),
+           "fmm_solve_host")
+
+
+def fmm_plan_set_precision(plan, mode):
+    _check(lib().fmm_plan_set_precision(plan, int(mode)), "fmm_plan_set_precision")
+
+
+def fmm_plan_get_shape(plan):
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib().fmm_plan_get_shape(plan, *[ctypes.byref(x) for x in v]), "fmm_plan_get_shape")
+    return tuple(x.value for x in v)
+
+
+def fmm_plan_copy_stage(plan, stage, level, dst, stream=None):
+    _check(lib().fmm_plan_copy_stage(plan, int(stage), int(level), dst.data_ptr(), dst.numel(),
+                                     _stream_of(dst, stream)), "fmm_plan_copy_stage")
+
+
+def fmm_plan_set_timing(plan, enable):
+    _check(lib().fmm_plan_set_timing(plan, int(bool(enable))), "fmm_plan_set_timing")
+
+
+def fmm_plan_stage_times(plan):
+    buf = (ctypes.c_float * FMM_TIME_SLOTS)()
+    _check(lib().fmm_plan_stage_times(plan, buf, FMM_TIME_SLOTS), "fmm_plan_stage_times")
+    return list(buf)
+
+
+class Plan:
+    """Owning wrapper: ``Plan(N, L, order).solve(rho) -> (phi, accel)``."""
+
+    def __init__(self, N, L, order, precision=FMM_PREC_FP32):
+        self.handle = fmm_plan_create(N, L, order)
+        self.N, self.L, self.order, self.S = fmm_plan_get_shape(self.handle)
+        if precision != FMM_PREC_FP32:
+            fmm_plan_set_precision(self.handle, precision)
+
+    def set_precision(self, mode):
+        fmm_plan_set_precision(self.handle, mode)
+
+    def solve(self, density, potential=None, accel=None, stream=None):
+        import torch
+        n = self.N
+        if potential is None:
+            potential = torch.empty((n, n, n), dtype=torch.float32, device=density.device)
+        if accel is None:
+            accel = torch.empty((3, n, n, n), dtype=torch.float32, device=density.device)
+        fmm_solve(self.handle, density, potential, accel, stream)
+        return potential, accel
+
+    def stage(self, stage, level):
+        import torch
+        p3 = self.order ** 3
+        if stage == FMM_STAGE_MEAN:
+            out = torch.empty(1, dtype=torch.float32, device="cuda")
+        else:
+            k = p3 if stage == FMM_STAGE_MULTIPOLE else 4 * p3
+            out = torch.empty((8 ** level) * k, dtype=torch.float32, device="cuda")
+        fmm_plan_copy_stage(self.handle, stage, level, out)
+        return out
+
+    def close(self):
+        if self.handle:
+            fmm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

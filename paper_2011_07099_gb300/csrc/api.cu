@@ -1,0 +1,350 @@
+// The C-ABI of libfmm: plan lifecycle, solve orchestration and errors.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <set>
+#include <tuple>
+#include <vector>
+
+#include "fmm_internal.cuh"
+
+using fmm::Plan;
+
+namespace {
+
+thread_local int g_last_error = FMM_OK;
+
+int set_err(int code) {
+  g_last_error = code;
+  return code;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+#define FMM_CUDA_TRY(expr)                  \
+  do {                                      \
+    cudaError_t _e = (expr);                \
+    if (_e != cudaSuccess) {                \
+      return set_err(FMM_ERR_CUDA);         \
+    }                                       \
+  } while (0)
+
+// 1-D Lagrange basis on the gridlet points X_j = (j + 1/2)/p (node-size units)
+// evaluated at the K cell-centred points y_k = (k + 1/2)/K: w[s][k] = l_s(y_k).
+// This is the separable solution of the Sec. 2 Vandermonde system (the
+// gridlet masses that keep every multipole Q_n, n_i < p).  Computed in double.
+std::vector<float> lagrange_weights(int p, int K) {
+  std::vector<float> w((size_t)p * K);
+  for (int s = 0; s < p; ++s) {
+    const double xs = (s + 0.5) / p;
+    for (int k = 0; k < K; ++k) {
+      const double y = (k + 0.5) / K;
+      double v = 1.0;
+      for (int j = 0; j < p; ++j) {
+        if (j == s) continue;
+        const double xj = (j + 0.5) / p;
+        v *= (y - xj) / (xs - xj);
+      }
+      w[(size_t)s * K + k] = (float)v;
+    }
+  }
+  return w;
+}
+
+// Interaction-zone offsets o = T - S (node units, nearest periodic image) for
+// the node whose position in its parent is c = cx | cy << 1 | cz << 2: the
+// children of the parent's periodic neighbours minus the node's own periodic
+// neighbours (Sec. 2, Fig. fmm).  Under periodic wrap every node with the same
+// position in its parent has the translated list, so one list per child type.
+std::vector<int8_t> interaction_offsets(int level, int c) {
+  const int n = 1 << level, np = n >> 1;
+  auto wrapn = [](int v, int m) { return ((v % m) + m) % m; };
+  const int tx = c & 1, ty = (c >> 1) & 1, tz = (c >> 2) & 1;   // parent is (0,0,0)
+  std::set<std::tuple<int, int, int>> kids, near;
+  for (int a = -1; a <= 1; ++a)
+    for (int b = -1; b <= 1; ++b)
+      for (int d = -1; d <= 1; ++d) {
+        const int qx = wrapn(a, np), qy = wrapn(b, np), qz = wrapn(d, np);
+        for (int i = 0; i < 8; ++i)
+          kids.insert(std::make_tuple(2 * qx + (i & 1), 2 * qy + ((i >> 1) & 1), 2 * qz + (i >> 2)));
+        near.insert(std::make_tuple(wrapn(tx + a, n), wrapn(ty + b, n), wrapn(tz + d, n)));
+      }
+  std::vector<int8_t> out;
+  for (const auto& k : kids) {
+    if (near.count(k)) continue;
+    int o[3] = {tx - std::get<0>(k), ty - std::get<1>(k), tz - std::get<2>(k)};
+    for (int& v : o) {
+      v = wrapn(v, n);
+      if (v > n / 2) v -= n;          // nearest image; +n/2 kept (G_S1 is 1-periodic)
+    }
+    out.push_back((int8_t)o[0]);
+    out.push_back((int8_t)o[1]);
+    out.push_back((int8_t)o[2]);
+  }
+  return out;
+}
+
+void free_plan(Plan* P) {
+  if (!P) return;
+  cudaFree(P->d_partials);
+  cudaFree(P->d_mean);
+  for (int l = 0; l <= fmm::kMaxLevel; ++l) {
+    cudaFree(P->M[l]);
+    cudaFree(P->F[l]);
+    cudaFree(P->tab[l]);
+    cudaFree(P->offsets[l]);
+  }
+  cudaFree(P->near_tab);
+  cudaFree(P->w_p2m);
+  cudaFree(P->w_m2m);
+  cudaFree(P->stage_in);
+  cudaFree(P->stage_out);
+  for (auto& e : P->ev)
+    if (e) cudaEventDestroy(e);
+  delete P;
+}
+
+template <typename T>
+bool dev_alloc(T** ptr, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(ptr), sizeof(T) * count) == cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fmm_last_error(void) { return g_last_error; }
+
+const char* fmm_error_string(int code) {
+  switch (code) {
+    case FMM_OK: return "ok";
+    case FMM_ERR_ARG: return "invalid argument";
+    case FMM_ERR_CUDA: return "CUDA runtime error";
+    case FMM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case FMM_ERR_INTERNAL: return "internal consistency check failed";
+    case FMM_ERR_ALLOC: return "allocation failed";
+    case FMM_ERR_UNSUPPORTED: return "unsupported by this build";
+    default: return "unknown error code";
+  }
+}
+
+fmm_plan* fmm_plan_create(int N, int L, int order) {
+  if (L < 2 || L > fmm::kMaxLevel || order < 1 || order > fmm::kMaxOrder || N <= 0) {
+    set_err(FMM_ERR_ARG);
+    return nullptr;
+  }
+  const int n = 1 << L;
+  if (N % n != 0) {
+    set_err(FMM_ERR_ARG);
+    return nullptr;
+  }
+  const int S = N / n;
+  if (S != 1 && S != 2 && S != 4 && S != 8) {
+    set_err(FMM_ERR_ARG);
+    return nullptr;
+  }
+  Plan* P = new (std::nothrow) Plan();
+  if (!P) {
+    set_err(FMM_ERR_ALLOC);
+    return nullptr;
+  }
+  P->N = N;
+  P->L = L;
+  P->p = order;
+  P->S = S;
+  if (cudaGetDevice(&P->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess) {
+    delete P;
+    set_err(FMM_ERR_CUDA);
+    return nullptr;
+  }
+  const int p = order, p3 = p * p * p;
+  bool ok = true;
+  P->n_partials = 4 * P->num_sms;
+  ok = ok && dev_alloc(&P->d_partials, P->n_partials) && dev_alloc(&P->d_mean, 1);
+  for (int l = 2; l <= L && ok; ++l) {
+    const size_t nodes = (size_t)1 << (3 * l);
+    const size_t E = 8 * p - 1;
+    ok = dev_alloc(&P->M[l], nodes * p3) && dev_alloc(&P->F[l], nodes * 4 * p3) &&
+         dev_alloc(&P->tab[l], E * E * E);
+  }
+  ok = ok && dev_alloc(&P->near_tab, (size_t)8 * S * S * S) && dev_alloc(&P->w_p2m, (size_t)p * S) &&
+       dev_alloc(&P->w_m2m, (size_t)p * 2 * p);
+  if (!ok) {
+    free_plan(P);
+    set_err(FMM_ERR_ALLOC);
+    return nullptr;
+  }
+  // host-side constants: Lagrange weights and interaction lists
+  std::vector<float> wp = lagrange_weights(p, S), wm = lagrange_weights(p, 2 * p);
+  bool cok = cudaMemcpy(P->w_p2m, wp.data(), wp.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(P->w_m2m, wm.data(), wm.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+  for (int l = 2; l <= L && cok; ++l) {
+    std::vector<int8_t> all;
+    int count = -1;
+    for (int c = 0; c < 8; ++c) {
+      std::vector<int8_t> o = interaction_offsets(l, c);
+      const int k = (int)o.size() / 3;
+      if (count >= 0 && k != count) cok = false;
+      count = k;
+      all.insert(all.end(), o.begin(), o.end());
+    }
+    P->n_off[l] = count;
+    cok = cok && (l == 2 ? count == 37 : count == 189);
+    cok = cok && dev_alloc(&P->offsets[l], all.size()) &&
+          cudaMemcpy(P->offsets[l], all.data(), all.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  if (!cok) {
+    free_plan(P);
+    set_err(FMM_ERR_INTERNAL);
+    return nullptr;
+  }
+  if (fmm::launch_tables(*P, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    free_plan(P);
+    set_err(FMM_ERR_CUDA);
+    return nullptr;
+  }
+  set_err(FMM_OK);
+  return reinterpret_cast<fmm_plan*>(P);
+}
+
+void fmm_plan_destroy(fmm_plan* plan) {
+  if (!plan) return;
+  cudaDeviceSynchronize();
+  free_plan(reinterpret_cast<Plan*>(plan));
+}
+
+int fmm_plan_get_shape(const fmm_plan* plan, int* N, int* L, int* order, int* S) {
+  if (!plan) return set_err(FMM_ERR_ARG);
+  const Plan* P = reinterpret_cast<const Plan*>(plan);
+  if (N) *N = P->N;
+  if (L) *L = P->L;
+  if (order) *order = P->p;
+  if (S) *S = P->S;
+  return set_err(FMM_OK);
+}
+
+int fmm_plan_set_precision(fmm_plan* plan, int mode) {
+  if (!plan) return set_err(FMM_ERR_ARG);
+  if (mode != FMM_PREC_FP32) return set_err(mode == FMM_PREC_BF16 || mode == FMM_PREC_BF16X3 ? FMM_ERR_UNSUPPORTED : FMM_ERR_ARG);
+  reinterpret_cast<Plan*>(plan)->prec = mode;
+  return set_err(FMM_OK);
+}
+
+int fmm_plan_set_timing(fmm_plan* plan, int enable) {
+  if (!plan) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  if (enable && !P.ev[0]) {
+    for (auto& e : P.ev) FMM_CUDA_TRY(cudaEventCreate(&e));
+  }
+  P.timing = enable ? 1 : 0;
+  return set_err(FMM_OK);
+}
+
+int fmm_plan_stage_times(fmm_plan* plan, float* ms, int n) {
+  if (!plan || !ms || n < 0) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  if (!P.timed) return set_err(FMM_ERR_ARG);
+  const int k = n < FMM_TIME_SLOTS ? n : FMM_TIME_SLOTS;
+  for (int i = 0; i < k; ++i) {
+    ms[i] = 0.f;
+    if (i == FMM_TIME_M2M && P.L <= 2) continue;
+    if (i == FMM_TIME_L2L && P.L <= 2) continue;
+    if (i >= FMM_TIME_M2L_LEVEL0 && (i - FMM_TIME_M2L_LEVEL0 < 2 || i - FMM_TIME_M2L_LEVEL0 > P.L)) continue;
+    FMM_CUDA_TRY(cudaEventSynchronize(P.ev[2 * i + 1]));
+    FMM_CUDA_TRY(cudaEventElapsedTime(&ms[i], P.ev[2 * i], P.ev[2 * i + 1]));
+  }
+  return set_err(FMM_OK);
+}
+
+int fmm_solve(fmm_plan* plan, const float* density, float* potential, float* accel, void* stream) {
+  if (!plan || !density || !potential || !accel) return set_err(FMM_ERR_ARG);
+  if (!aligned16(density) || !aligned16(potential) || !aligned16(accel)) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool t = P.timing != 0;
+  auto mark = [&](int slot, int end) -> cudaError_t {
+    return t ? cudaEventRecord(P.ev[2 * slot + end], s) : cudaSuccess;
+  };
+  FMM_CUDA_TRY(mark(FMM_TIME_MEAN, 0));
+  FMM_CUDA_TRY(fmm::launch_mean(P, density, s));
+  FMM_CUDA_TRY(mark(FMM_TIME_MEAN, 1));
+  FMM_CUDA_TRY(mark(FMM_TIME_P2M, 0));
+  FMM_CUDA_TRY(fmm::launch_p2m(P, density, s));
+  FMM_CUDA_TRY(mark(FMM_TIME_P2M, 1));
+  FMM_CUDA_TRY(mark(FMM_TIME_M2M, 0));
+  for (int l = P.L - 1; l >= 2; --l) FMM_CUDA_TRY(fmm::launch_m2m(P, l, s));
+  FMM_CUDA_TRY(mark(FMM_TIME_M2M, 1));
+  FMM_CUDA_TRY(mark(FMM_TIME_M2L, 0));
+  for (int l = 2; l <= P.L; ++l) {
+    FMM_CUDA_TRY(mark(FMM_TIME_M2L_LEVEL0 + l, 0));
+    FMM_CUDA_TRY(fmm::launch_m2l_fp32(P, l, s));
+    FMM_CUDA_TRY(mark(FMM_TIME_M2L_LEVEL0 + l, 1));
+  }
+  FMM_CUDA_TRY(mark(FMM_TIME_M2L, 1));
+  FMM_CUDA_TRY(mark(FMM_TIME_L2L, 0));
+  for (int l = 2; l < P.L; ++l) FMM_CUDA_TRY(fmm::launch_l2l(P, l, s));
+  FMM_CUDA_TRY(mark(FMM_TIME_L2L, 1));
+  FMM_CUDA_TRY(mark(FMM_TIME_P2P, 0));
+  FMM_CUDA_TRY(fmm::launch_p2p(P, density, potential, accel, s));
+  FMM_CUDA_TRY(mark(FMM_TIME_P2P, 1));
+  P.solved = 1;
+  if (t) P.timed = 1;
+  return set_err(FMM_OK);
+}
+
+int fmm_solve_host(fmm_plan* plan, const float* density_host, float* potential_host, float* accel_host,
+                   void* stream) {
+  if (!plan || !density_host || !potential_host || !accel_host) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  const size_t n3 = (size_t)P.N * P.N * P.N;
+  if (!P.stage_in) {
+    if (!dev_alloc(&P.stage_in, n3) || !dev_alloc(&P.stage_out, 4 * n3)) return set_err(FMM_ERR_ALLOC);
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  FMM_CUDA_TRY(cudaMemcpyAsync(P.stage_in, density_host, n3 * sizeof(float), cudaMemcpyHostToDevice, s));
+  int rc = fmm_solve(plan, P.stage_in, P.stage_out, P.stage_out + n3, stream);
+  if (rc != FMM_OK) return rc;
+  FMM_CUDA_TRY(cudaMemcpyAsync(potential_host, P.stage_out, n3 * sizeof(float), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA_TRY(cudaMemcpyAsync(accel_host, P.stage_out + n3, 3 * n3 * sizeof(float), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA_TRY(cudaStreamSynchronize(s));
+  return set_err(FMM_OK);
+}
+
+int fmm_plan_copy_stage(fmm_plan* plan, int stage, int level, float* dst, size_t count, void* stream) {
+  if (!plan || !dst) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t p3 = (size_t)P.p * P.p * P.p;
+  if (stage == FMM_STAGE_MEAN) {
+    if (count < 1) return set_err(FMM_ERR_ARG);
+    // one-value conversion through the host keeps this path free of extra kernels
+    double m = 0.0;
+    FMM_CUDA_TRY(cudaMemcpyAsync(&m, P.d_mean, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FMM_CUDA_TRY(cudaStreamSynchronize(s));
+    const float mf = (float)m;
+    FMM_CUDA_TRY(cudaMemcpyAsync(dst, &mf, sizeof(float), cudaMemcpyHostToDevice, s));
+    FMM_CUDA_TRY(cudaStreamSynchronize(s));
+    return set_err(FMM_OK);
+  }
+  if (level < 2 || level > P.L) return set_err(FMM_ERR_ARG);
+  const size_t nodes = (size_t)1 << (3 * level);
+  const float* src = nullptr;
+  size_t need = 0;
+  if (stage == FMM_STAGE_MULTIPOLE) {
+    src = P.M[level];
+    need = nodes * p3;
+  } else if (stage == FMM_STAGE_LOCAL) {
+    src = P.F[level];
+    need = nodes * 4 * p3;
+  } else {
+    return set_err(FMM_ERR_ARG);
+  }
+  if (count < need) return set_err(FMM_ERR_ARG);
+  FMM_CUDA_TRY(cudaMemcpyAsync(dst, src, need * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return set_err(FMM_OK);
+}
+
+}  // extern "C"

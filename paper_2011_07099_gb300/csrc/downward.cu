@@ -1,0 +1,49 @@
+// Downward pass: L2L (eq. fmm3).
+//
+// The local field of a child is the parent's local field projected with the
+// transpose of the child's M2M matrix: Phi_child[q] = sum_r T_{r q} Phi_parent[r]
+// (Sec. 3 eq. fmm3).  With T the separable Lagrange matrix, that is the parent
+// field interpolated at the child's gridlet points.  The 8 children's points
+// form one uniform (2p)^3 mesh over the parent, so one CTA expands all four
+// fields of a parent onto that mesh and adds them to the children's fields
+// (which already hold their own M2L result).
+#include "fmm_internal.cuh"
+
+namespace fmm {
+namespace {
+
+__global__ void k_l2l(const float* __restrict__ Fp, int p, const float* __restrict__ w, float* __restrict__ Fc) {
+  extern __shared__ float sm[];
+  const int K = 2 * p, p3 = p * p * p;
+  float* W = sm;                         // p*K  ([p][2p], used transposed)
+  float* in = W + p * K;                 // 4*p^3
+  float* t1 = in + 4 * p3;               // 4*p*p*K
+  float* t2 = t1 + 4 * p * p * K;        // 4*p*K*K
+  float* out = t2 + 4 * p * K * K;       // 4*K^3
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int i = tid; i < p * K; i += nthr) W[i] = w[i];
+  const float* src = Fp + (size_t)blockIdx.x * 4 * p3;
+  for (int i = tid; i < 4 * p3; i += nthr) in[i] = src[i];
+  __syncthreads();
+  contract3(in, t1, t2, out, 4, p, K, W, K, true, tid, nthr);
+  float* dst = Fc + (size_t)blockIdx.x * 8 * 4 * p3;
+  for (int i = tid; i < 8 * 4 * p3; i += nthr) {
+    const int c = i / (4 * p3), rem = i % (4 * p3);
+    const int f = rem / p3, q = rem % p3;
+    const int qx = q % p, qy = (q / p) % p, qz = q / (p * p);
+    const int ux = (c & 1) * p + qx, uy = ((c >> 1) & 1) * p + qy, uz = (c >> 2) * p + qz;
+    dst[i] += out[((f * K + uz) * K + uy) * K + ux];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_l2l(Plan& P, int level, cudaStream_t s) {
+  const int p = P.p, K = 2 * p, p3 = p * p * p;
+  const size_t smem = sizeof(float) * (p * K + 4 * p3 + 4 * p * p * K + 4 * p * K * K + 4 * K * K * K);
+  const unsigned parents = 1u << (3 * level);
+  k_l2l<<<parents, 256, smem, s>>>(P.F[level], p, P.w_m2m, P.F[level + 1]);
+  return cudaGetLastError();
+}
+
+}  // namespace fmm

@@ -1,0 +1,118 @@
+// Internal declarations of libfmm (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "../../include/fmm.h"
+
+namespace fmm {
+
+constexpr int kMaxLevel = 8;
+constexpr int kMaxOrder = 8;
+constexpr int kFields = 4;          // Phi, g_x, g_y, g_z
+constexpr int kMaxOffsets = 189;    // interaction-zone size below level 2 (Sec. 2)
+
+// ---------------------------------------------------------------- Morton keys
+// Node order at every level is Morton: bit 3b of the key is bit b of x, 3b+1
+// of y, 3b+2 of z.  The 8 children of parent key P are 8P + c with
+// c = cx | cy << 1 | cz << 2, so siblings are contiguous.
+__host__ __device__ inline uint32_t spread3(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+__host__ __device__ inline uint32_t compact3(uint32_t v) {
+  v &= 0x09249249u;
+  v = (v ^ (v >> 2)) & 0x030C30C3u;
+  v = (v ^ (v >> 4)) & 0x0300F00Fu;
+  v = (v ^ (v >> 8)) & 0xFF0000FFu;
+  v = (v ^ (v >> 16)) & 0x000003FFu;
+  return v;
+}
+__host__ __device__ inline uint32_t morton(uint32_t x, uint32_t y, uint32_t z) {
+  return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+__host__ __device__ inline void unmorton(uint32_t k, uint32_t& x, uint32_t& y, uint32_t& z) {
+  x = compact3(k);
+  y = compact3(k >> 1);
+  z = compact3(k >> 2);
+}
+
+// ------------------------------------------------------------------- the plan
+struct Plan {
+  int N = 0, L = 0, p = 0, S = 0;
+  int prec = FMM_PREC_FP32;
+  int device = 0;
+  int num_sms = 0;
+  int solved = 0;
+
+  // device buffers
+  double* d_partials = nullptr;     // block partial sums for the mean
+  double* d_mean = nullptr;         // mean density (1 value)
+  int n_partials = 0;
+  float* M[kMaxLevel + 1] = {};     // gridlet masses, 8^l x p^3, levels 2..L
+  float* F[kMaxLevel + 1] = {};     // local fields, 8^l x 4 x p^3, levels 2..L
+  float4* tab[kMaxLevel + 1] = {};  // (G, -dG/dx, -dG/dy, -dG/dz) at n dx_l, n in [-(4p-1), 4p-1]^3
+  float4* near_tab = nullptr;       // the same at cell spacing for |d_i| in [0, 2S-1], folded
+  float* w_p2m = nullptr;           // Lagrange weights [p][S]: gridlet s at cell c
+  float* w_m2m = nullptr;           // Lagrange weights [p][2p]: parent s at child point u
+  int8_t* offsets[kMaxLevel + 1] = {};  // per level: [8 child types][n_off][3] (dx, dy, dz) = T - S
+  int n_off[kMaxLevel + 1] = {};
+
+  // per-stage timing: ev[2*k] / ev[2*k+1] bracket slot k
+  int timing = 0;
+  int timed = 0;
+  cudaEvent_t ev[2 * FMM_TIME_SLOTS] = {};
+
+  // host-buffer staging for fmm_solve_host
+  float* stage_in = nullptr;
+  float* stage_out = nullptr;
+};
+
+// ------------------------------------------------------------ kernel launchers
+// Each returns cudaGetLastError() after the launch.
+cudaError_t launch_tables(Plan& P, cudaStream_t s);
+cudaError_t launch_mean(Plan& P, const float* rho, cudaStream_t s);
+cudaError_t launch_p2m(Plan& P, const float* rho, cudaStream_t s);
+cudaError_t launch_m2m(Plan& P, int level, cudaStream_t s);       // level+1 -> level
+cudaError_t launch_m2l_fp32(Plan& P, int level, cudaStream_t s);  // writes F[level]
+cudaError_t launch_l2l(Plan& P, int level, cudaStream_t s);       // F[level] -> F[level+1] (adds)
+cudaError_t launch_p2p(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s);
+
+// Block-wide separable contraction over the middle axis of a [A][Kin][B]
+// array: out[a][s][b] = sum_k W(s,k) in[a][k][b], W(s,k) = W[s*ldw+k] or, when
+// wt is set, W[k*ldw+s].  Threads tid..nthr stride over the outputs.
+__device__ inline void contract_mid(const float* __restrict__ in, float* __restrict__ out, int A,
+                                    int Kin, int Kout, int B, const float* __restrict__ W, int ldw,
+                                    bool wt, int tid, int nthr) {
+  const int total = A * Kout * B;
+  for (int i = tid; i < total; i += nthr) {
+    const int b = i % B;
+    const int s = (i / B) % Kout;
+    const int a = i / (B * Kout);
+    const float* src = in + (size_t)a * Kin * B + b;
+    float acc = 0.f;
+    for (int k = 0; k < Kin; ++k) acc = fmaf(wt ? W[k * ldw + s] : W[s * ldw + k], src[k * B], acc);
+    out[i] = acc;
+  }
+}
+
+// 3-D separable contraction of `nf` fields [nf][Kin][Kin][Kin] -> [nf][Kout]^3,
+// the same 1-D matrix on every axis.  t1, t2 are scratch of nf*Kin*Kin*Kout
+// and nf*Kin*Kout*Kout floats.  Ends with __syncthreads().
+__device__ inline void contract3(const float* in, float* t1, float* t2, float* out, int nf, int Kin,
+                                 int Kout, const float* W, int ldw, bool wt, int tid, int nthr) {
+  contract_mid(in, t1, nf * Kin * Kin, Kin, Kout, 1, W, ldw, wt, tid, nthr);
+  __syncthreads();
+  contract_mid(t1, t2, nf * Kin, Kin, Kout, Kout, W, ldw, wt, tid, nthr);
+  __syncthreads();
+  contract_mid(t2, out, nf, Kin, Kout, Kout * Kout, W, ldw, wt, tid, nthr);
+  __syncthreads();
+}
+
+}  // namespace fmm

@@ -1,0 +1,153 @@
+// M2L on CUDA cores in FP32 (the plain form).
+//
+// Eq. fmm2 (Sec. 3): for a target node T at level l and every source node S
+// of its interaction zone (the children of the parent's neighbours that are
+// not T's neighbours, with periodic wrap, Sec. 2),
+//   Phi_T[r] += sum_s G(d + dx_l (r - s)) M_S[s],   d = (T - S) H_l,
+// and the three acceleration fields with -grad G.  Since H_l = p dx_l every
+// argument is dx_l (o p + r - s) with o = T - S in node units, so each
+// offset's translation matrix is a window of the level table.
+//
+// Work split: a CTA owns kNT targets of one child type (the 8 types have
+// different interaction lists, Sec. 2 Fig. fmm); thread r owns one target
+// gridlet point and keeps kNT x 4 accumulators.  Per offset the CTA stages the
+// (2p-1)^3 table window and the kNT source gridlets in shared memory, so every
+// table value read feeds 4 x kNT FMAs and every mass read (a broadcast) feeds 4.
+#include "fmm_internal.cuh"
+
+namespace fmm {
+namespace {
+
+constexpr int kNT = 16;   // targets per CTA
+
+template <int P>
+__global__ void __launch_bounds__(((P * P * P + 31) / 32) * 32 < 64 ? 64 : ((P * P * P + 31) / 32) * 32)
+k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __restrict__ tab,
+           const int8_t* __restrict__ offs, int n_off, int level) {
+  constexpr int P3 = P * P * P;
+  constexpr int D = 2 * P - 1;          // table window per dimension
+  constexpr int D3 = D * D * D;
+  constexpr int HW = 4 * P - 1, E = 8 * P - 1;
+  extern __shared__ float4 sm4[];
+  float4* win = sm4;                                     // D3 float4
+  float4* msrc = win + D3;                               // P3 x (kNT/4) float4: [s][k]
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int ctype = blockIdx.y;
+  const int n = 1 << level;
+  const uint32_t n_par = 1u << (3 * (level - 1));
+  const uint32_t par0 = blockIdx.x * kNT;
+  const int8_t* my_offs = offs + (size_t)ctype * n_off * 3;
+
+  // target coordinates for the loads
+  __shared__ int tx[kNT], ty[kNT], tz[kNT];
+  if (tid < kNT) {
+    uint32_t x = 0, y = 0, z = 0;
+    if (par0 + tid < n_par) unmorton(8u * (par0 + tid) + ctype, x, y, z);
+    tx[tid] = x; ty[tid] = y; tz[tid] = z;
+  }
+
+  float acc[4][kNT];
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int k = 0; k < kNT; ++k) acc[f][k] = 0.f;
+
+  const int r = tid;
+  const int rx = r % P, ry = (r / P) % P, rz = r / (P * P);
+  const int rbase = ((rz + P - 1) * D + (ry + P - 1)) * D + (rx + P - 1);
+
+  for (int io = 0; io < n_off; ++io) {
+    const int ox = my_offs[3 * io + 0], oy = my_offs[3 * io + 1], oz = my_offs[3 * io + 2];
+    __syncthreads();   // previous offset's compute is done with the buffers (and tx.. are set)
+    for (int i = tid; i < D3; i += nthr) {
+      const int dx = i % D - (P - 1), dy = (i / D) % D - (P - 1), dz = i / (D * D) - (P - 1);
+      const int nx = ox * P + dx + HW, ny = oy * P + dy + HW, nz = oz * P + dz + HW;
+      win[i] = __ldg(tab + ((size_t)nz * E + ny) * E + nx);
+    }
+    float* ms = reinterpret_cast<float*>(msrc);
+    for (int i = tid; i < kNT * P3; i += nthr) {
+      const int k = i / P3, s = i % P3;
+      float v = 0.f;
+      if (par0 + k < n_par) {
+        const uint32_t sx = (uint32_t)(tx[k] - ox) & (n - 1), sy = (uint32_t)(ty[k] - oy) & (n - 1),
+                       sz = (uint32_t)(tz[k] - oz) & (n - 1);
+        v = __ldg(M + (size_t)morton(sx, sy, sz) * P3 + s);
+      }
+      ms[s * kNT + k] = v;
+    }
+    __syncthreads();
+    if (r < P3) {
+#pragma unroll 1
+      for (int sz = 0; sz < P; ++sz) {
+#pragma unroll 1
+        for (int sy = 0; sy < P; ++sy) {
+#pragma unroll
+          for (int sx = 0; sx < P; ++sx) {
+            const int s = (sz * P + sy) * P + sx;
+            const float4 t = win[rbase - ((sz * D + sy) * D + sx)];
+            const float4* mv = msrc + s * (kNT / 4);
+#pragma unroll
+            for (int q = 0; q < kNT / 4; ++q) {
+              const float4 m = mv[q];
+              const float mm[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                acc[0][4 * q + j] = fmaf(t.x, mm[j], acc[0][4 * q + j]);
+                acc[1][4 * q + j] = fmaf(t.y, mm[j], acc[1][4 * q + j]);
+                acc[2][4 * q + j] = fmaf(t.z, mm[j], acc[2][4 * q + j]);
+                acc[3][4 * q + j] = fmaf(t.w, mm[j], acc[3][4 * q + j]);
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  if (r < P3) {
+#pragma unroll
+    for (int k = 0; k < kNT; ++k) {
+      if (par0 + k >= n_par) break;
+      float* dst = F + (size_t)(8u * (par0 + k) + ctype) * 4 * P3;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) dst[f * P3 + r] = acc[f][k];
+    }
+  }
+}
+
+template <int P>
+cudaError_t launch_p(Plan& Pl, int level, cudaStream_t s) {
+  constexpr int P3 = P * P * P;
+  constexpr int D = 2 * P - 1;
+  int threads = ((P3 + 31) / 32) * 32;
+  if (threads < 64) threads = 64;
+  const size_t smem = sizeof(float4) * (D * D * D + P3 * (kNT / 4));
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_m2l_fp32<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const uint32_t n_par = 1u << (3 * (level - 1));
+  dim3 grid((n_par + kNT - 1) / kNT, 8);
+  k_m2l_fp32<P><<<grid, threads, smem, s>>>(Pl.M[level], Pl.F[level], Pl.tab[level], Pl.offsets[level],
+                                            Pl.n_off[level], level);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_m2l_fp32(Plan& P, int level, cudaStream_t s) {
+  switch (P.p) {
+    case 1: return launch_p<1>(P, level, s);
+    case 2: return launch_p<2>(P, level, s);
+    case 3: return launch_p<3>(P, level, s);
+    case 4: return launch_p<4>(P, level, s);
+    case 5: return launch_p<5>(P, level, s);
+    case 6: return launch_p<6>(P, level, s);
+    case 7: return launch_p<7>(P, level, s);
+    case 8: return launch_p<8>(P, level, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace fmm

@@ -1,0 +1,88 @@
+// Green's-function tabulation (plan time, FP64 arithmetic).
+//
+// G_S1 of eq. gfs1 (Sec. 4): G(x) = -1/(4 pi |xhat|) with
+//   xhat_i = xi(x_i),  xi(t) = (9/(8 pi)) sin(pi t) - (1/(24 pi)) sin(3 pi t),
+// the Sec. 3 ansatz with n = 1, a_1 = -1/8.  xi is odd-periodic, so |xhat| and
+// G are 1-periodic and the wrap of xhat is a no-op.  Gradient by the chain
+// rule: dG/dx_i = xhat_i xi'(x_i) / (4 pi |xhat|^3), xi'(t) = (9/8) cos(pi t) -
+// (1/8) cos(3 pi t).  Tables hold (G, -dG/dx, -dG/dy, -dG/dz) so that a
+// contraction with masses yields (Phi, g) directly, g = -grad Phi.
+#include "fmm_internal.cuh"
+
+namespace fmm {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+// Mean of 1/r over the unit cube: 3 ln(2 + sqrt 3) - pi/2.  The paper does not
+// define the self term G(0); the cell-averaged Newtonian value is used.
+__device__ inline double cube_mean_inv_r() { return 3.0 * log(2.0 + sqrt(3.0)) - 0.5 * kPi; }
+
+__device__ inline double xi_s1(double t) {
+  return (9.0 / (8.0 * kPi)) * sinpi(t) - (1.0 / (24.0 * kPi)) * sinpi(3.0 * t);
+}
+__device__ inline double dxi_s1(double t) { return 1.125 * cospi(t) - 0.125 * cospi(3.0 * t); }
+
+// (G, -grad G) at x; the caller handles x == 0.
+__device__ inline void gs1(double x, double y, double z, double out[4]) {
+  const double hx = xi_s1(x), hy = xi_s1(y), hz = xi_s1(z);
+  const double r2 = hx * hx + hy * hy + hz * hz;
+  const double r = sqrt(r2);
+  const double inv4pi = 1.0 / (4.0 * kPi);
+  out[0] = -inv4pi / r;
+  const double c = -inv4pi / (r2 * r);
+  out[1] = c * hx * dxi_s1(x);
+  out[2] = c * hy * dxi_s1(y);
+  out[3] = c * hz * dxi_s1(z);
+}
+
+// M2L table of level l: n in [-(4p-1), 4p-1]^3 at spacing dx_l = 1/(2^l p)
+// (Sec. 3: gridlet spacing of a level-l node; the (4 N_g)^D samples of Sec. 4
+// folded over the sign of each component).  Entry n = 0 is never used by M2L
+// (the interaction zone excludes near nodes) and is stored as 0.
+__global__ void k_tab_m2l(float4* __restrict__ out, int p, int level) {
+  const int hw = 4 * p - 1, E = 8 * p - 1;
+  const long total = (long)E * E * E;
+  const double dx = 1.0 / ((double)(1 << level) * p);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % E) - hw, iy = (int)((i / E) % E) - hw, iz = (int)(i / ((long)E * E)) - hw;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (ix | iy | iz) gs1(ix * dx, iy * dx, iz * dx, v);
+    out[i] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+  }
+}
+
+// Near-zone table at cell spacing h = 1/N for |d_i| in [0, 2S-1] (the offsets
+// between a cell of a leaf and a cell of any of its 27 neighbour leaves),
+// folded: G is even in every component, -dG/dx_i is odd in x_i and even in the
+// others, so entries hold the values at (|dx|, |dy|, |dz|) and the kernel
+// restores the signs.  d = 0 holds the self term -(1/4 pi) <1/r>_cell / h.
+__global__ void k_tab_near(float4* __restrict__ out, int S, int N) {
+  const int D = 2 * S;
+  const int total = D * D * D;
+  const double h = 1.0 / N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int ix = i % D, iy = (i / D) % D, iz = i / (D * D);
+    double v[4];
+    if (ix | iy | iz) {
+      gs1(ix * h, iy * h, iz * h, v);
+    } else {
+      v[0] = -cube_mean_inv_r() * (double)N / (4.0 * kPi);
+      v[1] = v[2] = v[3] = 0.0;
+    }
+    out[i] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_tables(Plan& P, cudaStream_t s) {
+  for (int l = 2; l <= P.L; ++l) {
+    k_tab_m2l<<<4 * P.num_sms, 256, 0, s>>>(P.tab[l], P.p, l);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_tab_near<<<P.num_sms, 256, 0, s>>>(P.near_tab, P.S, P.N);
+  return cudaGetLastError();
+}
+
+}  // namespace fmm

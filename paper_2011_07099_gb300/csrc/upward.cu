@@ -1,0 +1,125 @@
+// Upward pass: mean removal, P2M at the leaves and M2M up to level 2.
+//
+// Gridlet masses (Sec. 2): a node's order^3 effective masses on its
+// cell-centred mini-mesh must reproduce every Cartesian multipole Q_n,
+// n_i < order, of the mass they stand for.  The unique solution of that
+// Vandermonde system is separable: M_s = sum_c l_s(x_c) m_c with l_s the 1-D
+// Lagrange basis on the gridlet points, one factor per axis.  M2M (eq. fmm1)
+// is the same map with the children's gridlet points as sources: the 8 child
+// gridlets form a uniform (2 order)^3 cell-centred mesh over the parent.
+#include "fmm_internal.cuh"
+
+namespace fmm {
+namespace {
+
+// a0: block partial sums of the density in FP64.
+__global__ void k_partial_sum(const float4* __restrict__ rho4, size_t n4, double* __restrict__ partials) {
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = __ldg(rho4 + i);
+    acc += ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    acc = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) partials[blockIdx.x] = acc;
+  }
+}
+
+__global__ void k_final_mean(const double* __restrict__ partials, int n, double inv_cells, double* __restrict__ mean) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    acc = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) *mean = acc * inv_cells;
+  }
+}
+
+// a3: one CTA per leaf (Morton key = blockIdx.x).  Cell masses
+// m = (rho - mean) / N^3 are formed in FP64 and rounded once to FP32.
+__global__ void k_p2m(const float* __restrict__ rho, const double* __restrict__ mean, int N, int S, int p,
+                      const float* __restrict__ w, float* __restrict__ Mout) {
+  extern __shared__ float sm[];
+  float* W = sm;                       // p*S
+  float* in = W + p * S;               // S^3
+  float* t1 = in + S * S * S;          // S*S*p
+  float* t2 = t1 + S * S * p;          // S*p*p
+  float* out = t2 + S * p * p;         // p^3
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  uint32_t lx, ly, lz;
+  unmorton(blockIdx.x, lx, ly, lz);
+  const double mu = *mean;
+  const double inv_vol = 1.0 / ((double)N * N * N);
+  for (int i = tid; i < p * S; i += nthr) W[i] = w[i];
+  for (int i = tid; i < S * S * S; i += nthr) {
+    const int cx = i % S, cy = (i / S) % S, cz = i / (S * S);
+    const size_t g = ((size_t)(lz * S + cz) * N + (ly * S + cy)) * N + (lx * S + cx);
+    in[i] = (float)(((double)rho[g] - mu) * inv_vol);
+  }
+  __syncthreads();
+  contract3(in, t1, t2, out, 1, S, p, W, S, false, tid, nthr);
+  const int p3 = p * p * p;
+  for (int i = tid; i < p3; i += nthr) Mout[(size_t)blockIdx.x * p3 + i] = out[i];
+}
+
+// a4: one CTA per parent; the 8 children (keys 8P + c) are gathered into a
+// (2p)^3 mesh and contracted with the [p][2p] Lagrange matrix on each axis.
+__global__ void k_m2m(const float* __restrict__ Mc, int p, const float* __restrict__ w, float* __restrict__ Mp) {
+  extern __shared__ float sm[];
+  const int K = 2 * p, p3 = p * p * p;
+  float* W = sm;                // p*K
+  float* in = W + p * K;        // K^3
+  float* t1 = in + K * K * K;   // K*K*p
+  float* t2 = t1 + K * K * p;   // K*p*p
+  float* out = t2 + K * p * p;  // p^3
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int i = tid; i < p * K; i += nthr) W[i] = w[i];
+  const float* src = Mc + (size_t)blockIdx.x * 8 * p3;
+  for (int i = tid; i < 8 * p3; i += nthr) {
+    const int c = i / p3, q = i % p3;
+    const int qx = q % p, qy = (q / p) % p, qz = q / (p * p);
+    const int ux = (c & 1) * p + qx, uy = ((c >> 1) & 1) * p + qy, uz = (c >> 2) * p + qz;
+    in[(uz * K + uy) * K + ux] = src[i];
+  }
+  __syncthreads();
+  contract3(in, t1, t2, out, 1, K, p, W, K, false, tid, nthr);
+  for (int i = tid; i < p3; i += nthr) Mp[(size_t)blockIdx.x * p3 + i] = out[i];
+}
+
+}  // namespace
+
+cudaError_t launch_mean(Plan& P, const float* rho, cudaStream_t s) {
+  const size_t n4 = (size_t)P.N * P.N * P.N / 4;
+  k_partial_sum<<<P.n_partials, 256, 0, s>>>(reinterpret_cast<const float4*>(rho), n4, P.d_partials);
+  k_final_mean<<<1, 1024, 0, s>>>(P.d_partials, P.n_partials, 1.0 / ((double)P.N * P.N * P.N), P.d_mean);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_p2m(Plan& P, const float* rho, cudaStream_t s) {
+  const int S = P.S, p = P.p;
+  const size_t smem = sizeof(float) * (p * S + S * S * S + S * S * p + S * p * p + p * p * p);
+  const unsigned leaves = 1u << (3 * P.L);
+  k_p2m<<<leaves, 128, smem, s>>>(rho, P.d_mean, P.N, S, p, P.w_p2m, P.M[P.L]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_m2m(Plan& P, int level, cudaStream_t s) {
+  const int p = P.p, K = 2 * p;
+  const size_t smem = sizeof(float) * (p * K + K * K * K + K * K * p + K * p * p + p * p * p);
+  const unsigned parents = 1u << (3 * level);
+  k_m2m<<<parents, 128, smem, s>>>(P.M[level + 1], p, P.w_m2m, P.M[level]);
+  return cudaGetLastError();
+}
+
+}  // namespace fmm

@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads and exports every declared symbol (no GPU).
+
+No compute call is made here: without a GPU only loading and symbol lookup
+are checked, plus the argument validation that fails before touching the
+device.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2011_07099_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(fmm_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.lib()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert declared, "no declarations found"
+    for name in declared:
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (fmm_[a-z0-9_]+)", out))
+    assert declared <= exported
+    assert declared == set(binding.SIGNATURES), "binding and header disagree"
+
+
+def test_error_strings(lib):
+    for code in range(7):
+        assert binding.lib().fmm_error_string(code)
+    assert binding.lib().fmm_error_string(99) == b"unknown error code"
+
+
+@pytest.mark.parametrize("args", [(32, 1, 2), (32, 9, 2), (30, 3, 2), (32, 3, 0), (32, 3, 9), (512, 3, 4), (0, 2, 2)])
+def test_plan_create_rejects_bad_shapes_before_touching_the_device(lib, args):
+    # sizes are validated on the host first: S must be 1, 2, 4 or 8, 2 <= L <= 8, 1 <= order <= 8
+    assert binding.lib().fmm_plan_create(*args) is None
+    assert binding.lib().fmm_last_error() == binding.FMM_ERR_ARG
+
+
+def test_null_plan_calls_fail_cleanly(lib):
+    L = binding.lib()
+    assert L.fmm_solve(None, None, None, None, None) == binding.FMM_ERR_ARG
+    assert L.fmm_plan_set_precision(None, 0) == binding.FMM_ERR_ARG
+    L.fmm_plan_destroy(None)
