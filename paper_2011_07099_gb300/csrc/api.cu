@@ -35,8 +35,8 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 // evaluated at the K cell-centred points y_k = (k + 1/2)/K: w[s][k] = l_s(y_k).
 // This is the separable solution of the Sec. 2 Vandermonde system (the
 // gridlet masses that keep every multipole Q_n, n_i < p).  Computed in double.
-std::vector<float> lagrange_weights(int p, int K) {
-  std::vector<float> w((size_t)p * K);
+std::vector<double> lagrange_weights(int p, int K) {
+  std::vector<double> w((size_t)p * K);
   for (int s = 0; s < p; ++s) {
     const double xs = (s + 0.5) / p;
     for (int k = 0; k < K; ++k) {
@@ -47,7 +47,7 @@ std::vector<float> lagrange_weights(int p, int K) {
         const double xj = (j + 0.5) / p;
         v *= (y - xj) / (xs - xj);
       }
-      w[(size_t)s * K + k] = (float)v;
+      w[(size_t)s * K + k] = v;
     }
   }
   return w;
@@ -94,11 +94,14 @@ void free_plan(Plan* P) {
     cudaFree(P->M[l]);
     cudaFree(P->F[l]);
     cudaFree(P->tab[l]);
+    cudaFree(P->tab_lo[l]);
     cudaFree(P->offsets[l]);
   }
   cudaFree(P->near_tab);
   cudaFree(P->w_p2m);
   cudaFree(P->w_m2m);
+  cudaFree(P->wd_p2m);
+  cudaFree(P->wd_m2m);
   cudaFree(P->stage_in);
   cudaFree(P->stage_out);
   for (auto& e : P->ev)
@@ -169,18 +172,32 @@ fmm_plan* fmm_plan_create(int N, int L, int order) {
     const size_t E = 8 * p - 1;
     ok = dev_alloc(&P->M[l], nodes * p3) && dev_alloc(&P->F[l], nodes * 4 * p3) &&
          dev_alloc(&P->tab[l], E * E * E);
+    if (ok && l <= fmm::kExtTopLevel) ok = dev_alloc(&P->tab_lo[l], E * E * E);
   }
   ok = ok && dev_alloc(&P->near_tab, (size_t)8 * S * S * S) && dev_alloc(&P->w_p2m, (size_t)p * S) &&
-       dev_alloc(&P->w_m2m, (size_t)p * 2 * p);
+       dev_alloc(&P->w_m2m, (size_t)p * 2 * p) && dev_alloc(&P->wd_p2m, (size_t)p * S) &&
+       dev_alloc(&P->wd_m2m, (size_t)p * 2 * p);
   if (!ok) {
     free_plan(P);
     set_err(FMM_ERR_ALLOC);
     return nullptr;
   }
   // host-side constants: Lagrange weights and interaction lists
-  std::vector<float> wp = lagrange_weights(p, S), wm = lagrange_weights(p, 2 * p);
-  bool cok = cudaMemcpy(P->w_p2m, wp.data(), wp.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(P->w_m2m, wm.data(), wm.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+  // FP64 weights for the upward pass, (hi, lo) FP32 pairs for the downward pass
+  std::vector<double> wp = lagrange_weights(p, S), wm = lagrange_weights(p, 2 * p);
+  auto split = [](const std::vector<double>& v) {
+    std::vector<float2> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+      const float hi = (float)v[i];
+      o[i] = make_float2(hi, (float)(v[i] - (double)hi));
+    }
+    return o;
+  };
+  std::vector<float2> wp2 = split(wp), wm2 = split(wm);
+  bool cok = cudaMemcpy(P->w_p2m, wp2.data(), wp2.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(P->w_m2m, wm2.data(), wm2.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(P->wd_p2m, wp.data(), wp.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(P->wd_m2m, wm.data(), wm.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
   for (int l = 2; l <= L && cok; ++l) {
     std::vector<int8_t> all;
     int count = -1;
@@ -201,7 +218,9 @@ fmm_plan* fmm_plan_create(int N, int L, int order) {
     set_err(FMM_ERR_INTERNAL);
     return nullptr;
   }
-  if (fmm::launch_tables(*P, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+  if (fmm::setup_upward(*P) != cudaSuccess || fmm::setup_m2l_fp32(*P) != cudaSuccess ||
+      fmm::setup_downward(*P) != cudaSuccess || fmm::setup_p2p(*P) != cudaSuccess ||
+      fmm::launch_tables(*P, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
     free_plan(P);
     set_err(FMM_ERR_CUDA);
     return nullptr;

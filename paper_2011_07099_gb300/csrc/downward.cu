@@ -12,11 +12,11 @@
 namespace fmm {
 namespace {
 
-__global__ void k_l2l(const float* __restrict__ Fp, int p, const float* __restrict__ w, float* __restrict__ Fc) {
-  extern __shared__ float sm[];
+__global__ void k_l2l(const float* __restrict__ Fp, int p, const float2* __restrict__ w, float* __restrict__ Fc) {
+  extern __shared__ float2 sm2[];
   const int K = 2 * p, p3 = p * p * p;
-  float* W = sm;                         // p*K  ([p][2p], used transposed)
-  float* in = W + p * K;                 // 4*p^3
+  float2* W = sm2;                       // p*K  ([p][2p], used transposed)
+  float* in = reinterpret_cast<float*>(W + p * K);   // 4*p^3
   float* t1 = in + 4 * p3;               // 4*p*p*K
   float* t2 = t1 + 4 * p * p * K;        // 4*p*K*K
   float* out = t2 + 4 * p * K * K;       // 4*K^3
@@ -38,9 +38,13 @@ __global__ void k_l2l(const float* __restrict__ Fp, int p, const float* __restri
 
 }  // namespace
 
+cudaError_t setup_downward(const Plan& P) {
+  return cudaFuncSetAttribute(k_l2l, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
 cudaError_t launch_l2l(Plan& P, int level, cudaStream_t s) {
   const int p = P.p, K = 2 * p, p3 = p * p * p;
-  const size_t smem = sizeof(float) * (p * K + 4 * p3 + 4 * p * p * K + 4 * p * K * K + 4 * K * K * K);
+  const size_t smem = sizeof(float2) * p * K + sizeof(float) * (4 * p3 + 4 * p * p * K + 4 * p * K * K + 4 * K * K * K);
   const unsigned parents = 1u << (3 * level);
   k_l2l<<<parents, 256, smem, s>>>(P.F[level], p, P.w_m2m, P.F[level + 1]);
   return cudaGetLastError();

@@ -13,6 +13,9 @@ constexpr int kMaxLevel = 8;
 constexpr int kMaxOrder = 8;
 constexpr int kFields = 4;          // Phi, g_x, g_y, g_z
 constexpr int kMaxOffsets = 189;    // interaction-zone size below level 2 (Sec. 2)
+// The top two far-field levels (2 and 3) carry the long-range potential, whose
+// sum cancels most; their Phi contraction uses G = hi + lo split tables.
+constexpr int kExtTopLevel = 3;
 
 // ---------------------------------------------------------------- Morton keys
 // Node order at every level is Morton: bit 3b of the key is bit b of x, 3b+1
@@ -58,9 +61,12 @@ struct Plan {
   float* M[kMaxLevel + 1] = {};     // gridlet masses, 8^l x p^3, levels 2..L
   float* F[kMaxLevel + 1] = {};     // local fields, 8^l x 4 x p^3, levels 2..L
   float4* tab[kMaxLevel + 1] = {};  // (G, -dG/dx, -dG/dy, -dG/dz) at n dx_l, n in [-(4p-1), 4p-1]^3
+  float* tab_lo[kMaxLevel + 1] = {};  // G - fl32(G) of the same entries (levels 2..kExtLevels+1)
   float4* near_tab = nullptr;       // the same at cell spacing for |d_i| in [0, 2S-1], folded
-  float* w_p2m = nullptr;           // Lagrange weights [p][S]: gridlet s at cell c
-  float* w_m2m = nullptr;           // Lagrange weights [p][2p]: parent s at child point u
+  float2* w_p2m = nullptr;          // Lagrange weights [p][S] as (hi, lo): gridlet s at cell c
+  float2* w_m2m = nullptr;          // Lagrange weights [p][2p] as (hi, lo): parent s at child point u
+  double* wd_p2m = nullptr;         // the same weights in FP64 for the upward pass
+  double* wd_m2m = nullptr;
   int8_t* offsets[kMaxLevel + 1] = {};  // per level: [8 child types][n_off][3] (dx, dy, dz) = T - S
   int n_off[kMaxLevel + 1] = {};
 
@@ -74,6 +80,14 @@ struct Plan {
   float* stage_out = nullptr;
 };
 
+// ------------------------------------------------------- per-plan kernel setup
+// Opt-in shared-memory limits (and other function attributes) are set once at
+// plan creation, never inside a solve, so a solve is safe to capture.
+cudaError_t setup_upward(const Plan& P);
+cudaError_t setup_m2l_fp32(const Plan& P);
+cudaError_t setup_downward(const Plan& P);
+cudaError_t setup_p2p(const Plan& P);
+
 // ------------------------------------------------------------ kernel launchers
 // Each returns cudaGetLastError() after the launch.
 cudaError_t launch_tables(Plan& P, cudaStream_t s);
@@ -86,9 +100,11 @@ cudaError_t launch_p2p(Plan& P, const float* rho, float* phi, float* acc, cudaSt
 
 // Block-wide separable contraction over the middle axis of a [A][Kin][B]
 // array: out[a][s][b] = sum_k W(s,k) in[a][k][b], W(s,k) = W[s*ldw+k] or, when
-// wt is set, W[k*ldw+s].  Threads tid..nthr stride over the outputs.
+// wt is set, W[k*ldw+s].  Threads tid..nthr stride over the outputs.  Weights
+// are (hi, lo) float pairs: the same weights apply to every node, so their
+// FP32 rounding would err coherently across the whole mesh.
 __device__ inline void contract_mid(const float* __restrict__ in, float* __restrict__ out, int A,
-                                    int Kin, int Kout, int B, const float* __restrict__ W, int ldw,
+                                    int Kin, int Kout, int B, const float2* __restrict__ W, int ldw,
                                     bool wt, int tid, int nthr) {
   const int total = A * Kout * B;
   for (int i = tid; i < total; i += nthr) {
@@ -96,17 +112,50 @@ __device__ inline void contract_mid(const float* __restrict__ in, float* __restr
     const int s = (i / B) % Kout;
     const int a = i / (B * Kout);
     const float* src = in + (size_t)a * Kin * B + b;
-    float acc = 0.f;
-    for (int k = 0; k < Kin; ++k) acc = fmaf(wt ? W[k * ldw + s] : W[s * ldw + k], src[k * B], acc);
+    float acc = 0.f, lo = 0.f;
+    for (int k = 0; k < Kin; ++k) {
+      const float2 w = wt ? W[k * ldw + s] : W[s * ldw + k];
+      const float x = src[k * B];
+      acc = fmaf(w.x, x, acc);
+      lo = fmaf(w.y, x, lo);
+    }
+    out[i] = acc + lo;
+  }
+}
+
+// FP64 variant for the upward pass: the cell masses of a mean-free field and
+// the partial sums of P2M/M2M cancel, and every node of a near-uniform region
+// rounds the same way in FP32, so those errors add up coherently across the
+// mesh instead of averaging out.
+__device__ inline void contract_mid_d(const double* __restrict__ in, double* __restrict__ out, int A, int Kin,
+                                      int Kout, int B, const double* __restrict__ W, int ldw, int tid, int nthr) {
+  const int total = A * Kout * B;
+  for (int i = tid; i < total; i += nthr) {
+    const int b = i % B;
+    const int s = (i / B) % Kout;
+    const int a = i / (B * Kout);
+    const double* src = in + (size_t)a * Kin * B + b;
+    double acc = 0.0;
+    for (int k = 0; k < Kin; ++k) acc = fma(W[s * ldw + k], src[k * B], acc);
     out[i] = acc;
   }
+}
+
+__device__ inline void contract3_d(const double* in, double* t1, double* t2, double* out, int Kin, int Kout,
+                                   const double* W, int ldw, int tid, int nthr) {
+  contract_mid_d(in, t1, Kin * Kin, Kin, Kout, 1, W, ldw, tid, nthr);
+  __syncthreads();
+  contract_mid_d(t1, t2, Kin, Kin, Kout, Kout, W, ldw, tid, nthr);
+  __syncthreads();
+  contract_mid_d(t2, out, 1, Kin, Kout, Kout * Kout, W, ldw, tid, nthr);
+  __syncthreads();
 }
 
 // 3-D separable contraction of `nf` fields [nf][Kin][Kin][Kin] -> [nf][Kout]^3,
 // the same 1-D matrix on every axis.  t1, t2 are scratch of nf*Kin*Kin*Kout
 // and nf*Kin*Kout*Kout floats.  Ends with __syncthreads().
 __device__ inline void contract3(const float* in, float* t1, float* t2, float* out, int nf, int Kin,
-                                 int Kout, const float* W, int ldw, bool wt, int tid, int nthr) {
+                                 int Kout, const float2* W, int ldw, bool wt, int tid, int nthr) {
   contract_mid(in, t1, nf * Kin * Kin, Kin, Kout, 1, W, ldw, wt, tid, nthr);
   __syncthreads();
   contract_mid(t1, t2, nf * Kin, Kin, Kout, Kout, W, ldw, wt, tid, nthr);

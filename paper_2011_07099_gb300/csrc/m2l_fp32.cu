@@ -8,49 +8,66 @@
 // argument is dx_l (o p + r - s) with o = T - S in node units, so each
 // offset's translation matrix is a window of the level table.
 //
-// Work split: a CTA owns kNT targets of one child type (the 8 types have
+// Work split: a CTA owns NT targets of one child type (the 8 types have
 // different interaction lists, Sec. 2 Fig. fmm); thread r owns one target
-// gridlet point and keeps kNT x 4 accumulators.  Per offset the CTA stages the
-// (2p-1)^3 table window and the kNT source gridlets in shared memory, so every
-// table value read feeds 4 x kNT FMAs and every mass read (a broadcast) feeds 4.
+// gridlet point and keeps NT x 4 accumulators.  Per offset the CTA stages the
+// (2p-1)^3 table window and the NT source gridlets in shared memory, so every
+// table value read feeds 4 x NT FMAs and every mass read (a broadcast) feeds 4.
+//
+// Rounding: the far-field sum cancels heavily (mean-free masses, G < 0), so a
+// plain running FP32 sum over all 189 p^3 terms loses several digits.  Within
+// one offset the terms of every field mostly share a sign (G < 0 and grad G
+// points one way across a distant node, while a node's gridlet masses mostly
+// share the sign of its net mass), so a running sum grows ~p^3 times larger
+// than a term.  The terms are therefore summed as a tree: p-term rows, rows
+// into planes, and each plane is added to the total with Kahan compensation.
+// At the top two levels the potential also takes the low half of the split
+// table, G = G_hi + G_lo: rounding G to FP32 errs coherently across targets
+// and is the largest remaining error of the long-range potential.
 #include "fmm_internal.cuh"
 
 namespace fmm {
 namespace {
 
-constexpr int kNT = 16;   // targets per CTA
-
 template <int P>
-__global__ void __launch_bounds__(((P * P * P + 31) / 32) * 32 < 64 ? 64 : ((P * P * P + 31) / 32) * 32)
+struct M2LShape {
+  static constexpr int P3 = P * P * P;
+  static constexpr int THREADS = ((P3 + 31) / 32) * 32 < 64 ? 64 : ((P3 + 31) / 32) * 32;
+  static constexpr int NT = P3 > 256 ? 4 : 8;            // targets per CTA (register budget)
+};
+
+template <int P, bool EXT>
+__global__ void __launch_bounds__(M2LShape<P>::THREADS)
 k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __restrict__ tab,
-           const int8_t* __restrict__ offs, int n_off, int level) {
+           const float* __restrict__ tab_lo, const int8_t* __restrict__ offs, int n_off, int level) {
   constexpr int P3 = P * P * P;
+  constexpr int NT = M2LShape<P>::NT;
   constexpr int D = 2 * P - 1;          // table window per dimension
   constexpr int D3 = D * D * D;
   constexpr int HW = 4 * P - 1, E = 8 * P - 1;
   extern __shared__ float4 sm4[];
   float4* win = sm4;                                     // D3 float4
-  float4* msrc = win + D3;                               // P3 x (kNT/4) float4: [s][k]
+  float4* msrc = win + D3;                               // P3 x (NT/4) float4: [s][k]
+  float* win_lo = reinterpret_cast<float*>(msrc + P3 * (NT / 4));   // D3 (EXT only)
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int ctype = blockIdx.y;
   const int n = 1 << level;
   const uint32_t n_par = 1u << (3 * (level - 1));
-  const uint32_t par0 = blockIdx.x * kNT;
+  const uint32_t par0 = blockIdx.x * NT;
   const int8_t* my_offs = offs + (size_t)ctype * n_off * 3;
 
-  // target coordinates for the loads
-  __shared__ int tx[kNT], ty[kNT], tz[kNT];
-  if (tid < kNT) {
+  __shared__ int tx[NT], ty[NT], tz[NT];
+  if (tid < NT) {
     uint32_t x = 0, y = 0, z = 0;
     if (par0 + tid < n_par) unmorton(8u * (par0 + tid) + ctype, x, y, z);
     tx[tid] = x; ty[tid] = y; tz[tid] = z;
   }
 
-  float acc[4][kNT];
+  float acc[4][NT], comp[4][NT];
 #pragma unroll
   for (int f = 0; f < 4; ++f)
 #pragma unroll
-    for (int k = 0; k < kNT; ++k) acc[f][k] = 0.f;
+    for (int k = 0; k < NT; ++k) acc[f][k] = comp[f][k] = 0.f;
 
   const int r = tid;
   const int rx = r % P, ry = (r / P) % P, rz = r / (P * P);
@@ -63,9 +80,10 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
       const int dx = i % D - (P - 1), dy = (i / D) % D - (P - 1), dz = i / (D * D) - (P - 1);
       const int nx = ox * P + dx + HW, ny = oy * P + dy + HW, nz = oz * P + dz + HW;
       win[i] = __ldg(tab + ((size_t)nz * E + ny) * E + nx);
+      if (EXT) win_lo[i] = __ldg(tab_lo + ((size_t)nz * E + ny) * E + nx);
     }
     float* ms = reinterpret_cast<float*>(msrc);
-    for (int i = tid; i < kNT * P3; i += nthr) {
+    for (int i = tid; i < NT * P3; i += nthr) {
       const int k = i / P3, s = i % P3;
       float v = 0.f;
       if (par0 + k < n_par) {
@@ -73,39 +91,73 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
                        sz = (uint32_t)(tz[k] - oz) & (n - 1);
         v = __ldg(M + (size_t)morton(sx, sy, sz) * P3 + s);
       }
-      ms[s * kNT + k] = v;
+      ms[s * NT + k] = v;
     }
     __syncthreads();
     if (r < P3) {
+      float plo[NT];
+#pragma unroll
+      for (int k = 0; k < NT; ++k) plo[k] = 0.f;
 #pragma unroll 1
       for (int sz = 0; sz < P; ++sz) {
+        float plane[4][NT];
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+          for (int k = 0; k < NT; ++k) plane[f][k] = 0.f;
 #pragma unroll 1
         for (int sy = 0; sy < P; ++sy) {
+          float row[4][NT];
+#pragma unroll
+          for (int f = 0; f < 4; ++f)
+#pragma unroll
+            for (int k = 0; k < NT; ++k) row[f][k] = 0.f;
 #pragma unroll
           for (int sx = 0; sx < P; ++sx) {
             const int s = (sz * P + sy) * P + sx;
-            const float4 t = win[rbase - ((sz * D + sy) * D + sx)];
-            const float4* mv = msrc + s * (kNT / 4);
+            const int w = rbase - ((sz * D + sy) * D + sx);
+            const float4 t = win[w];
+            const float tl = EXT ? win_lo[w] : 0.f;
+            const float4* mv = msrc + s * (NT / 4);
 #pragma unroll
-            for (int q = 0; q < kNT / 4; ++q) {
+            for (int q = 0; q < NT / 4; ++q) {
               const float4 m = mv[q];
               const float mm[4] = {m.x, m.y, m.z, m.w};
 #pragma unroll
               for (int j = 0; j < 4; ++j) {
-                acc[0][4 * q + j] = fmaf(t.x, mm[j], acc[0][4 * q + j]);
-                acc[1][4 * q + j] = fmaf(t.y, mm[j], acc[1][4 * q + j]);
-                acc[2][4 * q + j] = fmaf(t.z, mm[j], acc[2][4 * q + j]);
-                acc[3][4 * q + j] = fmaf(t.w, mm[j], acc[3][4 * q + j]);
+                row[0][4 * q + j] = fmaf(t.x, mm[j], row[0][4 * q + j]);
+                row[1][4 * q + j] = fmaf(t.y, mm[j], row[1][4 * q + j]);
+                row[2][4 * q + j] = fmaf(t.z, mm[j], row[2][4 * q + j]);
+                row[3][4 * q + j] = fmaf(t.w, mm[j], row[3][4 * q + j]);
+                if (EXT) plo[4 * q + j] = fmaf(tl, mm[j], plo[4 * q + j]);
               }
             }
           }
+#pragma unroll
+          for (int f = 0; f < 4; ++f)
+#pragma unroll
+            for (int k = 0; k < NT; ++k) plane[f][k] += row[f][k];
         }
+        // Kahan-compensated add of the plane partial into the total
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+          for (int k = 0; k < NT; ++k) {
+            const float y = plane[f][k] - comp[f][k];
+            const float t = acc[f][k] + y;
+            comp[f][k] = (t - acc[f][k]) - y;
+            acc[f][k] = t;
+          }
+      }
+      if (EXT) {
+#pragma unroll
+        for (int k = 0; k < NT; ++k) comp[0][k] -= plo[k];
       }
     }
   }
   if (r < P3) {
 #pragma unroll
-    for (int k = 0; k < kNT; ++k) {
+    for (int k = 0; k < NT; ++k) {
       if (par0 + k >= n_par) break;
       float* dst = F + (size_t)(8u * (par0 + k) + ctype) * 4 * P3;
 #pragma unroll
@@ -118,23 +170,43 @@ template <int P>
 cudaError_t launch_p(Plan& Pl, int level, cudaStream_t s) {
   constexpr int P3 = P * P * P;
   constexpr int D = 2 * P - 1;
-  int threads = ((P3 + 31) / 32) * 32;
-  if (threads < 64) threads = 64;
-  const size_t smem = sizeof(float4) * (D * D * D + P3 * (kNT / 4));
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_m2l_fp32<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  constexpr int NT = M2LShape<P>::NT;
+  const int threads = M2LShape<P>::THREADS;
+  const bool ext = level <= kExtTopLevel;
+  const size_t smem = sizeof(float4) * (D * D * D + P3 * (NT / 4)) + (ext ? sizeof(float) * D * D * D : 0);
   const uint32_t n_par = 1u << (3 * (level - 1));
-  dim3 grid((n_par + kNT - 1) / kNT, 8);
-  k_m2l_fp32<P><<<grid, threads, smem, s>>>(Pl.M[level], Pl.F[level], Pl.tab[level], Pl.offsets[level],
-                                            Pl.n_off[level], level);
+  dim3 grid((n_par + NT - 1) / NT, 8);
+  if (ext)
+    k_m2l_fp32<P, true><<<grid, threads, smem, s>>>(Pl.M[level], Pl.F[level], Pl.tab[level], Pl.tab_lo[level],
+                                                    Pl.offsets[level], Pl.n_off[level], level);
+  else
+    k_m2l_fp32<P, false><<<grid, threads, smem, s>>>(Pl.M[level], Pl.F[level], Pl.tab[level], nullptr,
+                                                     Pl.offsets[level], Pl.n_off[level], level);
   return cudaGetLastError();
 }
 
+template <int P>
+cudaError_t setup_p() {
+  cudaError_t e = cudaFuncSetAttribute(k_m2l_fp32<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_m2l_fp32<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
 }  // namespace
+
+cudaError_t setup_m2l_fp32(const Plan& P) {
+  switch (P.p) {
+    case 1: return setup_p<1>();
+    case 2: return setup_p<2>();
+    case 3: return setup_p<3>();
+    case 4: return setup_p<4>();
+    case 5: return setup_p<5>();
+    case 6: return setup_p<6>();
+    case 7: return setup_p<7>();
+    case 8: return setup_p<8>();
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_m2l_fp32(Plan& P, int level, cudaStream_t s) {
   switch (P.p) {

@@ -33,7 +33,7 @@ struct P2PShape {
 template <int S>
 __global__ void __launch_bounds__(P2PShape<S>::THREADS)
 k_p2p(const float* __restrict__ rho, const double* __restrict__ mean, int N, int p,
-      const float4* __restrict__ near_tab, const float* __restrict__ Fleaf, const float* __restrict__ wp2m,
+      const float4* __restrict__ near_tab, const float* __restrict__ Fleaf, const float2* __restrict__ wp2m,
       float* __restrict__ phi, float* __restrict__ acc_out, int region_floats) {
   using Sh = P2PShape<S>;
   constexpr int W = Sh::W, TD = Sh::TD, TS = Sh::TS, ROWS = Sh::ROWS, NZG = Sh::NZG;
@@ -53,8 +53,8 @@ k_p2p(const float* __restrict__ rho, const double* __restrict__ mean, int N, int
   }
   // L2P: far[f][cz][cy][cx] = sum_s l_s(cz) l_s(cy) l_s(cx) F[f][s]
   {
-    float* W8 = region;                   // p*S weights
-    float* in = W8 + p * S;               // 4*p^3
+    float2* W8 = reinterpret_cast<float2*>(region);   // p*S weights (region is 16-byte aligned)
+    float* in = reinterpret_cast<float*>(W8 + p * S); // 4*p^3
     float* t1 = in + 4 * p3;              // 4*p*p*S
     float* t2 = t1 + 4 * p * p * S;       // 4*p*S*S
     for (int i = tid; i < p * S; i += nthr) W8[i] = wp2m[i];
@@ -85,11 +85,20 @@ k_p2p(const float* __restrict__ rho, const double* __restrict__ mean, int N, int
 #pragma unroll
     for (int x = 0; x < S; ++x) a[f][x] = 0.f;
 
+  // Rounding: each source row's 3S terms go into a fresh row partial, rows into
+  // a plane partial, planes into the total, so no running FP32 sum is longer
+  // than 3S terms (a single running sum over the 27 S^3 sources loses about
+  // log10(sqrt(27 S^3)) more digits).
   if (zg < NZG) {
     for (int zp = zg; zp < W; zp += NZG) {
       const int dz = cz + S - zp;                         // target z - source z (cells)
       const int adz = dz < 0 ? -dz : dz;
       const float sz = dz > 0 ? 1.f : (dz < 0 ? -1.f : 0.f);
+      float pl[4][S];
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int x = 0; x < S; ++x) pl[f][x] = 0.f;
 #pragma unroll 1
       for (int yp = 0; yp < W; ++yp) {
         const int dy = cy + S - yp;
@@ -100,6 +109,11 @@ k_p2p(const float* __restrict__ rho, const double* __restrict__ mean, int N, int
 #pragma unroll
         for (int j = 0; j < TD; ++j) t[j] = trow[j];
         const float* mrow = win + (zp * W + yp) * W;
+        float rw[4][S];
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+          for (int x = 0; x < S; ++x) rw[f][x] = 0.f;
 #pragma unroll
         for (int xp = 0; xp < W; ++xp) {
           const float m = mrow[xp];
@@ -109,13 +123,21 @@ k_p2p(const float* __restrict__ rho, const double* __restrict__ mean, int N, int
             const int dx = x + S - xp;                    // compile-time after unrolling
             const int adx = dx < 0 ? -dx : dx;
             const float4 v = t[adx];
-            a[0][x] = fmaf(v.x, m, a[0][x]);
-            a[1][x] = dx >= 0 ? fmaf(v.y, m, a[1][x]) : fmaf(-v.y, m, a[1][x]);
-            a[2][x] = fmaf(v.z, my, a[2][x]);
-            a[3][x] = fmaf(v.w, mz, a[3][x]);
+            rw[0][x] = fmaf(v.x, m, rw[0][x]);
+            rw[1][x] = dx >= 0 ? fmaf(v.y, m, rw[1][x]) : fmaf(-v.y, m, rw[1][x]);
+            rw[2][x] = fmaf(v.z, my, rw[2][x]);
+            rw[3][x] = fmaf(v.w, mz, rw[3][x]);
           }
         }
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+          for (int x = 0; x < S; ++x) pl[f][x] += rw[f][x];
       }
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int x = 0; x < S; ++x) a[f][x] += pl[f][x];
     }
   }
   __syncthreads();   // window no longer needed: reuse the region for the reduction
@@ -152,21 +174,34 @@ cudaError_t launch_s(Plan& P, const float* rho, float* phi, float* acc, cudaStre
   using Sh = P2PShape<S>;
   const int p = P.p, p3 = p * p * p;
   const int win = Sh::W * Sh::W * Sh::W;
-  const int l2p = p * S + 4 * p3 + 4 * p * p * S + 4 * p * S * S;
+  const int l2p = 2 * p * S + 4 * p3 + 4 * p * p * S + 4 * p * S * S;
   const int red = Sh::NZG * 4 * S * Sh::ROWS;
   int region = win;
   if (l2p > region) region = l2p;
   if (red > region) region = red;
   const size_t smem = sizeof(float4) * Sh::TD * Sh::TD * Sh::TS + sizeof(float) * (4 * S * S * S + region);
-  cudaError_t e = cudaFuncSetAttribute(k_p2p<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   const unsigned leaves = 1u << (3 * P.L);
   k_p2p<S><<<leaves, Sh::THREADS, smem, s>>>(rho, P.d_mean, P.N, p, P.near_tab, P.F[P.L], P.w_p2m, phi, acc,
                                              region);
   return cudaGetLastError();
 }
 
+template <int S>
+cudaError_t setup_s() {
+  return cudaFuncSetAttribute(k_p2p<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+}
+
 }  // namespace
+
+cudaError_t setup_p2p(const Plan& P) {
+  switch (P.S) {
+    case 1: return setup_s<1>();
+    case 2: return setup_s<2>();
+    case 4: return setup_s<4>();
+    case 8: return setup_s<8>();
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_p2p(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s) {
   switch (P.S) {

@@ -39,7 +39,7 @@ __device__ inline void gs1(double x, double y, double z, double out[4]) {
 // (Sec. 3: gridlet spacing of a level-l node; the (4 N_g)^D samples of Sec. 4
 // folded over the sign of each component).  Entry n = 0 is never used by M2L
 // (the interaction zone excludes near nodes) and is stored as 0.
-__global__ void k_tab_m2l(float4* __restrict__ out, int p, int level) {
+__global__ void k_tab_m2l(float4* __restrict__ out, float* __restrict__ lo, int p, int level) {
   const int hw = 4 * p - 1, E = 8 * p - 1;
   const long total = (long)E * E * E;
   const double dx = 1.0 / ((double)(1 << level) * p);
@@ -48,6 +48,7 @@ __global__ void k_tab_m2l(float4* __restrict__ out, int p, int level) {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (ix | iy | iz) gs1(ix * dx, iy * dx, iz * dx, v);
     out[i] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+    if (lo) lo[i] = (float)(v[0] - (double)(float)v[0]);
   }
 }
 
@@ -77,7 +78,7 @@ __global__ void k_tab_near(float4* __restrict__ out, int S, int N) {
 
 cudaError_t launch_tables(Plan& P, cudaStream_t s) {
   for (int l = 2; l <= P.L; ++l) {
-    k_tab_m2l<<<4 * P.num_sms, 256, 0, s>>>(P.tab[l], P.p, l);
+    k_tab_m2l<<<4 * P.num_sms, 256, 0, s>>>(P.tab[l], P.tab_lo[l], P.p, l);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -47,15 +47,16 @@ __global__ void k_final_mean(const double* __restrict__ partials, int n, double 
 }
 
 // a3: one CTA per leaf (Morton key = blockIdx.x).  Cell masses
-// m = (rho - mean) / N^3 are formed in FP64 and rounded once to FP32.
+// m = (rho - mean) / N^3 and the contraction are FP64; the gridlet masses are
+// rounded once to FP32.
 __global__ void k_p2m(const float* __restrict__ rho, const double* __restrict__ mean, int N, int S, int p,
-                      const float* __restrict__ w, float* __restrict__ Mout) {
-  extern __shared__ float sm[];
-  float* W = sm;                       // p*S
-  float* in = W + p * S;               // S^3
-  float* t1 = in + S * S * S;          // S*S*p
-  float* t2 = t1 + S * S * p;          // S*p*p
-  float* out = t2 + S * p * p;         // p^3
+                      const double* __restrict__ w, float* __restrict__ Mout) {
+  extern __shared__ double smd[];
+  double* W = smd;                     // p*S
+  double* in = W + p * S;              // S^3
+  double* t1 = in + S * S * S;         // S*S*p
+  double* t2 = t1 + S * S * p;         // S*p*p
+  double* out = t2 + S * p * p;        // p^3
   const int tid = threadIdx.x, nthr = blockDim.x;
   uint32_t lx, ly, lz;
   unmorton(blockIdx.x, lx, ly, lz);
@@ -65,24 +66,24 @@ __global__ void k_p2m(const float* __restrict__ rho, const double* __restrict__ 
   for (int i = tid; i < S * S * S; i += nthr) {
     const int cx = i % S, cy = (i / S) % S, cz = i / (S * S);
     const size_t g = ((size_t)(lz * S + cz) * N + (ly * S + cy)) * N + (lx * S + cx);
-    in[i] = (float)(((double)rho[g] - mu) * inv_vol);
+    in[i] = ((double)rho[g] - mu) * inv_vol;
   }
   __syncthreads();
-  contract3(in, t1, t2, out, 1, S, p, W, S, false, tid, nthr);
+  contract3_d(in, t1, t2, out, S, p, W, S, tid, nthr);
   const int p3 = p * p * p;
-  for (int i = tid; i < p3; i += nthr) Mout[(size_t)blockIdx.x * p3 + i] = out[i];
+  for (int i = tid; i < p3; i += nthr) Mout[(size_t)blockIdx.x * p3 + i] = (float)out[i];
 }
 
 // a4: one CTA per parent; the 8 children (keys 8P + c) are gathered into a
 // (2p)^3 mesh and contracted with the [p][2p] Lagrange matrix on each axis.
-__global__ void k_m2m(const float* __restrict__ Mc, int p, const float* __restrict__ w, float* __restrict__ Mp) {
-  extern __shared__ float sm[];
+__global__ void k_m2m(const float* __restrict__ Mc, int p, const double* __restrict__ w, float* __restrict__ Mp) {
+  extern __shared__ double smd[];
   const int K = 2 * p, p3 = p * p * p;
-  float* W = sm;                // p*K
-  float* in = W + p * K;        // K^3
-  float* t1 = in + K * K * K;   // K*K*p
-  float* t2 = t1 + K * K * p;   // K*p*p
-  float* out = t2 + K * p * p;  // p^3
+  double* W = smd;              // p*K
+  double* in = W + p * K;       // K^3
+  double* t1 = in + K * K * K;  // K*K*p
+  double* t2 = t1 + K * K * p;  // K*p*p
+  double* out = t2 + K * p * p; // p^3
   const int tid = threadIdx.x, nthr = blockDim.x;
   for (int i = tid; i < p * K; i += nthr) W[i] = w[i];
   const float* src = Mc + (size_t)blockIdx.x * 8 * p3;
@@ -90,14 +91,20 @@ __global__ void k_m2m(const float* __restrict__ Mc, int p, const float* __restri
     const int c = i / p3, q = i % p3;
     const int qx = q % p, qy = (q / p) % p, qz = q / (p * p);
     const int ux = (c & 1) * p + qx, uy = ((c >> 1) & 1) * p + qy, uz = (c >> 2) * p + qz;
-    in[(uz * K + uy) * K + ux] = src[i];
+    in[(uz * K + uy) * K + ux] = (double)src[i];
   }
   __syncthreads();
-  contract3(in, t1, t2, out, 1, K, p, W, K, false, tid, nthr);
-  for (int i = tid; i < p3; i += nthr) Mp[(size_t)blockIdx.x * p3 + i] = out[i];
+  contract3_d(in, t1, t2, out, K, p, W, K, tid, nthr);
+  for (int i = tid; i < p3; i += nthr) Mp[(size_t)blockIdx.x * p3 + i] = (float)out[i];
 }
 
 }  // namespace
+
+cudaError_t setup_upward(const Plan& P) {
+  cudaError_t e = cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
 
 cudaError_t launch_mean(Plan& P, const float* rho, cudaStream_t s) {
   const size_t n4 = (size_t)P.N * P.N * P.N / 4;
@@ -108,17 +115,17 @@ cudaError_t launch_mean(Plan& P, const float* rho, cudaStream_t s) {
 
 cudaError_t launch_p2m(Plan& P, const float* rho, cudaStream_t s) {
   const int S = P.S, p = P.p;
-  const size_t smem = sizeof(float) * (p * S + S * S * S + S * S * p + S * p * p + p * p * p);
+  const size_t smem = sizeof(double) * (p * S + S * S * S + S * S * p + S * p * p + p * p * p);
   const unsigned leaves = 1u << (3 * P.L);
-  k_p2m<<<leaves, 128, smem, s>>>(rho, P.d_mean, P.N, S, p, P.w_p2m, P.M[P.L]);
+  k_p2m<<<leaves, 128, smem, s>>>(rho, P.d_mean, P.N, S, p, P.wd_p2m, P.M[P.L]);
   return cudaGetLastError();
 }
 
 cudaError_t launch_m2m(Plan& P, int level, cudaStream_t s) {
   const int p = P.p, K = 2 * p;
-  const size_t smem = sizeof(float) * (p * K + K * K * K + K * K * p + K * p * p + p * p * p);
+  const size_t smem = sizeof(double) * (p * K + K * K * K + K * K * p + K * p * p + p * p * p);
   const unsigned parents = 1u << (3 * level);
-  k_m2m<<<parents, 128, smem, s>>>(P.M[level + 1], p, P.w_m2m, P.M[level]);
+  k_m2m<<<parents, 128, smem, s>>>(P.M[level + 1], p, P.wd_m2m, P.M[level]);
   return cudaGetLastError();
 }
 

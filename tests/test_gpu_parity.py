@@ -149,3 +149,28 @@ def test_bad_pointers_are_rejected(B):
     assert rc == B.FMM_ERR_ARG
     with pytest.raises(B.FMMError):
         plan.stage(B.FMM_STAGE_LOCAL, 9)
+
+
+FULL = [
+    # (N, L, p, config, sampled leaves (z, y, x)): the 256^3 p = 6 headline
+    # workload and the 128^3 p = 4 Plummer-clump workload at full size, in the
+    # launch configuration the bench times; the oracle evaluates only the
+    # sampled leaves (whole upward pass, then each leaf's chain of ancestors).
+    (256, 5, 6, 5, [[0, 0, 0], [31, 31, 31], [5, 17, 30]]),
+    (128, 5, 4, 1, [[0, 0, 0], [31, 31, 31], [7, 20, 13]]),
+]
+
+
+@pytest.mark.parametrize("N,L,p,cfg,leaves", FULL)
+def test_full_size_sampled_leaves_match_oracle(B, N, L, p, cfg, leaves):
+    rho = inputs.config_density(cfg, n=N)
+    plan, phi, acc = _gpu_solve(B, rho, L, p)
+    leaves = np.array(leaves)
+    ref = ofmm.solve_at(rho, L, p, leaves)
+    S = N >> L
+    g = np.concatenate([phi[None], acc])
+    got = np.stack([g[:, a * S:(a + 1) * S, b * S:(b + 1) * S, c * S:(c + 1) * S].reshape(4, -1)
+                    for a, b, c in leaves])
+    assert _rel(got[:, 0], ref[:, 0]) <= TOL_FP32
+    assert _rel(got[:, 1:], ref[:, 1:]) <= TOL_FP32
+    plan.close()
