@@ -96,8 +96,37 @@ int fmm_solve_host(fmm_plan* plan, const float* density_host,
 
 /* ---- configuration ------------------------------------------------------ */
 
-/* Select the M2L arithmetic (FMM_PREC_*).  Takes effect at the next solve. */
+/* Select the M2L arithmetic (FMM_PREC_*).  Takes effect at the next solve.
+ * FMM_PREC_BF16 / FMM_PREC_BF16X3 apply to levels >= 4; levels 2 and 3 keep
+ * the FP32 split-table contraction (their long-range sums cancel most).  The
+ * first tensor-core selection allocates and tabulates the split BF16 tables
+ * and multipole buffers (synchronous).  Order 1 ignores the tensor-core modes.
+ * FMM_ERR_ARG for an unknown mode. */
 int fmm_plan_set_precision(fmm_plan* plan, int mode);
+
+/* Limit of every bounded device-side wait (pipeline barriers of the
+ * tensor-core M2L), in milliseconds, 1..600000; default 2000.  A wait that
+ * runs out makes its kernel skip the rest of its work, free its tensor
+ * memory and return; fmm_plan_check() then reports FMM_ERR_TIMEOUT. */
+int fmm_plan_set_timeout_ms(fmm_plan* plan, int ms);
+
+/* Test hook for the failure path (no GPU fault is involved):
+ * FMM_FAULT_TC_STALL makes the tensor-core MMA issuer of later solves do
+ * nothing, so the dependent bounded waits expire; FMM_FAULT_NONE clears it. */
+#define FMM_FAULT_NONE     0
+#define FMM_FAULT_TC_STALL 1
+int fmm_plan_inject_fault(fmm_plan* plan, int kind);
+
+/* Tensor-core M2L: number of interaction offsets (1..189) accumulated in one
+ * TMEM partial sum before it is added to the compensated FP32 total on the
+ * CUDA cores.  Smaller is more accurate, larger is faster; default 2.
+ * FMM_ERR_ARG outside 1..189. */
+int fmm_plan_set_m2l_group(fmm_plan* plan, int offsets_per_partial);
+
+/* Synchronise the device and read the plan's device error word: FMM_OK, or
+ * FMM_ERR_TIMEOUT if a bounded device-side wait of an earlier solve gave up
+ * (the word is then cleared).  Solves never block forever. */
+int fmm_plan_check(fmm_plan* plan);
 
 /* Query plan parameters: writes N, L, order, S (any pointer may be NULL). */
 int fmm_plan_get_shape(const fmm_plan* plan, int* N, int* L, int* order, int* S);

@@ -24,6 +24,9 @@ FMM_PREC_FP32 = 0
 FMM_PREC_BF16 = 1
 FMM_PREC_BF16X3 = 2
 
+FMM_FAULT_NONE = 0
+FMM_FAULT_TC_STALL = 1
+
 FMM_STAGE_MULTIPOLE = 0
 FMM_STAGE_LOCAL = 1
 FMM_STAGE_MEAN = 2
@@ -42,6 +45,10 @@ SIGNATURES = {
     "fmm_error_string": (ctypes.c_char_p, [_I]),
     "fmm_plan_copy_stage": (_I, [_VP, _I, _I, _FP, _SZ, _VP]),
     "fmm_plan_set_timing": (_I, [_VP, _I]),
+    "fmm_plan_check": (_I, [_VP]),
+    "fmm_plan_set_m2l_group": (_I, [_VP, _I]),
+    "fmm_plan_set_timeout_ms": (_I, [_VP, _I]),
+    "fmm_plan_inject_fault": (_I, [_VP, _I]),
     "fmm_plan_stage_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), _I]),
 }
 
@@ -121,6 +128,22 @@ def fmm_plan_get_shape(plan):
 def fmm_plan_copy_stage(plan, stage, level, dst, stream=None):
     _check(lib().fmm_plan_copy_stage(plan, int(stage), int(level), dst.data_ptr(), dst.numel(),
                                      _stream_of(dst, stream)), "fmm_plan_copy_stage")
+
+
+def fmm_plan_set_m2l_group(plan, offsets_per_partial):
+    _check(lib().fmm_plan_set_m2l_group(plan, int(offsets_per_partial)), "fmm_plan_set_m2l_group")
+
+
+def fmm_plan_set_timeout_ms(plan, ms):
+    _check(lib().fmm_plan_set_timeout_ms(plan, int(ms)), "fmm_plan_set_timeout_ms")
+
+
+def fmm_plan_inject_fault(plan, kind):
+    _check(lib().fmm_plan_inject_fault(plan, int(kind)), "fmm_plan_inject_fault")
+
+
+def fmm_plan_check(plan):
+    _check(lib().fmm_plan_check(plan), "fmm_plan_check")
 
 
 def fmm_plan_set_timing(plan, enable):

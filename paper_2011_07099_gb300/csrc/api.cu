@@ -98,6 +98,13 @@ void free_plan(Plan* P) {
     cudaFree(P->offsets[l]);
   }
   cudaFree(P->near_tab);
+  cudaFree(P->d_err);
+  for (int l = 0; l <= fmm::kMaxLevel; ++l) {
+    cudaFree(P->tab_bf[l]);
+    cudaFree(P->Mbf_hi[l]);
+    cudaFree(P->Mbf_lo[l]);
+    cudaFree(P->Apre[l]);
+  }
   cudaFree(P->w_p2m);
   cudaFree(P->w_m2m);
   cudaFree(P->wd_p2m);
@@ -166,7 +173,8 @@ fmm_plan* fmm_plan_create(int N, int L, int order) {
   const int p = order, p3 = p * p * p;
   bool ok = true;
   P->n_partials = 4 * P->num_sms;
-  ok = ok && dev_alloc(&P->d_partials, P->n_partials) && dev_alloc(&P->d_mean, 1);
+  ok = ok && dev_alloc(&P->d_partials, P->n_partials) && dev_alloc(&P->d_mean, 1) && dev_alloc(&P->d_err, 1) &&
+       cudaMemset(P->d_err, 0, sizeof(int)) == cudaSuccess;
   for (int l = 2; l <= L && ok; ++l) {
     const size_t nodes = (size_t)1 << (3 * l);
     const size_t E = 8 * p - 1;
@@ -219,6 +227,7 @@ fmm_plan* fmm_plan_create(int N, int L, int order) {
     return nullptr;
   }
   if (fmm::setup_upward(*P) != cudaSuccess || fmm::setup_m2l_fp32(*P) != cudaSuccess ||
+      fmm::setup_m2l_tc(*P) != cudaSuccess ||
       fmm::setup_downward(*P) != cudaSuccess || fmm::setup_p2p(*P) != cudaSuccess ||
       fmm::launch_tables(*P, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
     free_plan(P);
@@ -245,10 +254,67 @@ int fmm_plan_get_shape(const fmm_plan* plan, int* N, int* L, int* order, int* S)
   return set_err(FMM_OK);
 }
 
+namespace {
+// Tensor-core M2L buffers: split tables and split multipoles for every level
+// at or below kTcMinLevel.  Allocated and tabulated once, synchronously.
+int prepare_tc(Plan& P) {
+  if (P.tc_ready) return FMM_OK;
+  const size_t E = 8 * P.p - 1;
+  const size_t kp = (size_t)fmm::tc_padded_k(P.p);
+  for (int l = fmm::kTcMinLevel; l <= P.L; ++l) {
+    const size_t nodes = (size_t)1 << (3 * l);
+    if (!dev_alloc(&P.tab_bf[l], E * E * E) || cudaMalloc(&P.Mbf_hi[l], nodes * kp * 2 * 2) != cudaSuccess ||
+        cudaMalloc(&P.Apre[l], fmm::tc_apre_bytes(P.p)) != cudaSuccess)
+      return FMM_ERR_ALLOC;
+    if (fmm::launch_tab_bf16(P, l, 0) != cudaSuccess || fmm::launch_build_a(P, l, 0) != cudaSuccess)
+      return FMM_ERR_CUDA;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return FMM_ERR_CUDA;
+  P.tc_ready = 1;
+  return FMM_OK;
+}
+}  // namespace
+
 int fmm_plan_set_precision(fmm_plan* plan, int mode) {
   if (!plan) return set_err(FMM_ERR_ARG);
-  if (mode != FMM_PREC_FP32) return set_err(mode == FMM_PREC_BF16 || mode == FMM_PREC_BF16X3 ? FMM_ERR_UNSUPPORTED : FMM_ERR_ARG);
-  reinterpret_cast<Plan*>(plan)->prec = mode;
+  if (mode != FMM_PREC_FP32 && mode != FMM_PREC_BF16 && mode != FMM_PREC_BF16X3) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  if (mode != FMM_PREC_FP32 && P.p >= 2) {
+    const int rc = prepare_tc(P);
+    if (rc != FMM_OK) return set_err(rc);
+  }
+  P.prec = mode;
+  return set_err(FMM_OK);
+}
+
+int fmm_plan_set_timeout_ms(fmm_plan* plan, int ms) {
+  if (!plan || ms < 1 || ms > 600000) return set_err(FMM_ERR_ARG);
+  reinterpret_cast<Plan*>(plan)->wait_ns = (uint64_t)ms * 1000000ull;
+  return set_err(FMM_OK);
+}
+
+int fmm_plan_inject_fault(fmm_plan* plan, int kind) {
+  if (!plan || (kind != FMM_FAULT_NONE && kind != FMM_FAULT_TC_STALL)) return set_err(FMM_ERR_ARG);
+  reinterpret_cast<Plan*>(plan)->inject_stall = kind == FMM_FAULT_TC_STALL ? 1 : 0;
+  return set_err(FMM_OK);
+}
+
+int fmm_plan_set_m2l_group(fmm_plan* plan, int offsets_per_partial) {
+  if (!plan || offsets_per_partial < 1 || offsets_per_partial > fmm::kMaxOffsets) return set_err(FMM_ERR_ARG);
+  reinterpret_cast<Plan*>(plan)->tc_group = offsets_per_partial;
+  return set_err(FMM_OK);
+}
+
+int fmm_plan_check(fmm_plan* plan) {
+  if (!plan) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  int h = 0;
+  FMM_CUDA_TRY(cudaDeviceSynchronize());
+  FMM_CUDA_TRY(cudaMemcpy(&h, P.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    FMM_CUDA_TRY(cudaMemset(P.d_err, 0, sizeof(int)));
+    return set_err(FMM_ERR_TIMEOUT);
+  }
   return set_err(FMM_OK);
 }
 
@@ -297,9 +363,15 @@ int fmm_solve(fmm_plan* plan, const float* density, float* potential, float* acc
   for (int l = P.L - 1; l >= 2; --l) FMM_CUDA_TRY(fmm::launch_m2m(P, l, s));
   FMM_CUDA_TRY(mark(FMM_TIME_M2M, 1));
   FMM_CUDA_TRY(mark(FMM_TIME_M2L, 0));
+  const bool tc = P.prec != FMM_PREC_FP32 && P.tc_ready;
   for (int l = 2; l <= P.L; ++l) {
     FMM_CUDA_TRY(mark(FMM_TIME_M2L_LEVEL0 + l, 0));
-    FMM_CUDA_TRY(fmm::launch_m2l_fp32(P, l, s));
+    if (tc && l >= fmm::kTcMinLevel) {
+      FMM_CUDA_TRY(fmm::launch_split_bf16(P, l, s));
+      FMM_CUDA_TRY(fmm::launch_m2l_tc(P, l, P.prec, s));
+    } else {
+      FMM_CUDA_TRY(fmm::launch_m2l_fp32(P, l, s));
+    }
     FMM_CUDA_TRY(mark(FMM_TIME_M2L_LEVEL0 + l, 1));
   }
   FMM_CUDA_TRY(mark(FMM_TIME_M2L, 1));

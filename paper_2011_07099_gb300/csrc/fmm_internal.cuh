@@ -16,6 +16,9 @@ constexpr int kMaxOffsets = 189;    // interaction-zone size below level 2 (Sec.
 // The top two far-field levels (2 and 3) carry the long-range potential, whose
 // sum cancels most; their Phi contraction uses G = hi + lo split tables.
 constexpr int kExtTopLevel = 3;
+// Levels at or below kExtTopLevel always run the FP32 split-table kernel; the
+// tensor-core precision modes apply from kTcMinLevel down to the leaves.
+constexpr int kTcMinLevel = kExtTopLevel + 1;
 
 // ---------------------------------------------------------------- Morton keys
 // Node order at every level is Morton: bit 3b of the key is bit b of x, 3b+1
@@ -68,6 +71,16 @@ struct Plan {
   double* wd_p2m = nullptr;         // the same weights in FP64 for the upward pass
   double* wd_m2m = nullptr;
   int8_t* offsets[kMaxLevel + 1] = {};  // per level: [8 child types][n_off][3] (dx, dy, dz) = T - S
+  // tensor-core M2L (levels >= kTcMinLevel, allocated on the first mixed-precision solve)
+  uint4* tab_bf[kMaxLevel + 1] = {};       // per table entry, per field: bf16 hi | bf16 lo << 16
+  void* Mbf_hi[kMaxLevel + 1] = {};        // gridlet masses split into bf16 hi / lo (interleaved per 8), rows padded
+  void* Mbf_lo[kMaxLevel + 1] = {};        // unused (kept null)
+  void* Apre[kMaxLevel + 1] = {};          // precomputed split translation tiles per offset slot
+  int tc_group = 2;                        // offsets accumulated per TMEM partial before promotion
+  uint64_t wait_ns = 2000000000ull;        // limit of every bounded device-side wait
+  int inject_stall = 0;                    // test hook: tensor-core MMA issuer stalls
+  int tc_ready = 0;
+  int* d_err = nullptr;                    // device error word (bounded waits that gave up)
   int n_off[kMaxLevel + 1] = {};
 
   // per-stage timing: ev[2*k] / ev[2*k+1] bracket slot k
@@ -97,6 +110,13 @@ cudaError_t launch_m2m(Plan& P, int level, cudaStream_t s);       // level+1 -> 
 cudaError_t launch_m2l_fp32(Plan& P, int level, cudaStream_t s);  // writes F[level]
 cudaError_t launch_l2l(Plan& P, int level, cudaStream_t s);       // F[level] -> F[level+1] (adds)
 cudaError_t launch_p2p(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s);
+cudaError_t setup_m2l_tc(const Plan& P);
+cudaError_t launch_tab_bf16(Plan& P, int level, cudaStream_t s);
+cudaError_t launch_split_bf16(Plan& P, int level, cudaStream_t s);
+cudaError_t launch_m2l_tc(Plan& P, int level, int mode, cudaStream_t s);
+int tc_padded_k(int p);
+size_t tc_apre_bytes(int p);
+cudaError_t launch_build_a(Plan& P, int level, cudaStream_t s);
 
 // Block-wide separable contraction over the middle axis of a [A][Kin][B]
 // array: out[a][s][b] = sum_k W(s,k) in[a][k][b], W(s,k) = W[s*ldw+k] or, when

@@ -7,6 +7,8 @@
 // rule: dG/dx_i = xhat_i xi'(x_i) / (4 pi |xhat|^3), xi'(t) = (9/8) cos(pi t) -
 // (1/8) cos(3 pi t).  Tables hold (G, -dG/dx, -dG/dy, -dG/dz) so that a
 // contraction with masses yields (Phi, g) directly, g = -grad Phi.
+#include <cuda_bf16.h>
+
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -74,7 +76,33 @@ __global__ void k_tab_near(float4* __restrict__ out, int S, int N) {
   }
 }
 
+// The same level table split into BF16 hi + lo per field for the tensor-core
+// M2L: each uint32 holds hi in its low half and lo = bf16(v - hi) in its high
+// half, the four fields in the four words of a uint4.
+__global__ void k_tab_bf16(uint4* __restrict__ out, int p, int level) {
+  const int hw = 4 * p - 1, E = 8 * p - 1;
+  const long total = (long)E * E * E;
+  const double dx = 1.0 / ((double)(1 << level) * p);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % E) - hw, iy = (int)((i / E) % E) - hw, iz = (int)(i / ((long)E * E)) - hw;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (ix | iy | iz) gs1(ix * dx, iy * dx, iz * dx, v);
+    uint32_t w[4];
+    for (int f = 0; f < 4; ++f) {
+      const __nv_bfloat16 h = __double2bfloat16(v[f]);
+      const __nv_bfloat16 l = __double2bfloat16(v[f] - (double)__bfloat162float(h));
+      w[f] = (uint32_t)__bfloat16_as_ushort(h) | ((uint32_t)__bfloat16_as_ushort(l) << 16);
+    }
+    out[i] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_tab_bf16(Plan& P, int level, cudaStream_t s) {
+  k_tab_bf16<<<4 * P.num_sms, 256, 0, s>>>(P.tab_bf[level], P.p, level);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_tables(Plan& P, cudaStream_t s) {
   for (int l = 2; l <= P.L; ++l) {
