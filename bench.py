@@ -3,7 +3,10 @@
 
 One step = one full solve (mean removal, P2M, M2M, M2L at every level, L2L,
 L2P and the near-zone sum) of a seeded synthetic 256^3 density field,
-order p = 6, with the input already resident in HBM.  Prints ONE JSON line.
+order p = 6, with the input already resident in HBM.  The timed form is the
+mixed-precision one (tensor-core bf16x3 M2L at levels >= 4); the plain FP32
+form is timed on the same field in the same run, and the result's error
+against PM is stated.  Prints ONE JSON line.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
                     [--n 256 --L 5 --p 6 --precision fp32|bf16|bf16x3]
@@ -110,6 +113,11 @@ def workload_density(n, field):
     return inputs.lognormal(n, sigma=0.5, seed=5000 + field)
 
 
+# DRAM bytes (read + write) of one k_p2p launch from the ncu capture of the
+# current kernel in profiles/k_p2p_256cube_p6.md
+P2P_TRAFFIC = {(256, 5, 6): 419.4e6}
+
+
 def p2p_flops(N, L):
     S = N >> L
     return (8 ** L) * (S ** 3) * 27 * (S ** 3) * 8.0      # 4 FMA per pair
@@ -137,6 +145,22 @@ def cpu_baseline():
     return {"value": 64 ** 3 / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "seconds": dt,
             "sample": "full oracle solve of a 64^3 lognormal field, p=6, L=3 (S=8), numpy FP64 on all host cores"}
+
+
+def accuracy_vs_pm(rho, phi, acc):
+    """Part of the oracle leg: relative L2 of the timed solve's result against
+    PM with the same Green's function (FFT convolution, FP64 host) and,
+    secondary, against the spectral PM with G_K."""
+    import numpy as np
+    from oracle import green, pm
+    n = rho.shape[0]
+    m = pm.masses(rho.astype(np.float64))
+    pphi, pg = pm.pm(m, green.g_s1, green.grad_g_s1, green.self_term(n))
+    kphi, kg = pm.pm_gk(m)
+    rel = lambda a, b: float(np.linalg.norm(a.astype(np.float64) - b) / np.linalg.norm(b))
+    return {"vs_pm_gs1": {"phi": rel(phi, pphi), "g": rel(acc, pg)},
+            "vs_pm_gk": {"phi": rel(phi - phi.mean(), kphi - kphi.mean()), "g": rel(acc, kg)},
+            "note": "relative L2 over all cells; PM(G_S1) is the primary reference (same G in PM and FMM)"}
 
 
 def run_reference(args):
@@ -170,7 +194,47 @@ def run_reference(args):
     return 0
 
 
+def _time_solves(B, plan, rho, phi, acc, steps, warmup, l2_flush, stream, barrier, timing=True):
+    """W untimed solves, then `steps` solves each bracketed by CUDA events on
+    the launching stream, with an L2 flush (256 MB write) between them.
+    Returns (per-step ms list, per-step stage-time lists, wall seconds)."""
+    import torch
+    for _ in range(warmup):
+        plan.solve(rho, phi, acc)
+    torch.cuda.synchronize()
+    B.fmm_plan_set_timing(plan.handle, timing)
+    step_ms, stage = [], []
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for _ in range(steps):
+        l2_flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.solve(rho, phi, acc)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        if timing:
+            stage.append(B.fmm_plan_stage_times(plan.handle))
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    B.fmm_plan_set_timing(plan.handle, False)
+    B.fmm_plan_check(plan.handle)
+    return step_ms, stage, wall
+
+
+def launches_per_solve(L, tc):
+    # mean (2) + P2M + M2M per level + M2L per level (+ split kernel on tensor
+    # levels) + L2L per level + P2P
+    m2l = sum(2 if (tc and lev >= 4) else 1 for lev in range(2, L + 1))
+    return 2 + 1 + (L - 2) + m2l + (L - 2) + 1
+
+
 def run_ours(args):
+    import numpy as np
     import torch
     from paper_2011_07099_gb300 import binding, build
 
@@ -186,45 +250,26 @@ def run_ours(args):
     B = binding
     n, L, p = args.n, args.L, args.p
     prec = {"fp32": B.FMM_PREC_FP32, "bf16": B.FMM_PREC_BF16, "bf16x3": B.FMM_PREC_BF16X3}[args.precision]
-    plan = B.Plan(n, L, p)
-    if prec != B.FMM_PREC_FP32:
-        plan.set_precision(prec)
-    rho = torch.from_numpy(workload_density(n, rank)).to(dev)
-    phi = torch.empty((n, n, n), dtype=torch.float32, device=dev)
-    acc = torch.empty((3, n, n, n), dtype=torch.float32, device=dev)
-    l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
-    stream = torch.cuda.current_stream(dev)
-
-    for _ in range(args.warmup):
-        plan.solve(rho, phi, acc)
-    torch.cuda.synchronize()
-    B.fmm_plan_set_timing(plan.handle, True)
+    tc = prec != B.FMM_PREC_FP32
 
     def barrier():
         if ws > 1:
             import torch.distributed as dist
             dist.barrier()
 
-    step_ms, stage = [], []
-    launches_per_solve = 2 + 1 + (L - 2) + (L - 1) + (L - 2) + 1
-    barrier()
-    torch.cuda.synchronize()
-    wall0 = time.perf_counter()
+    rho_host = workload_density(n, rank)
+    rho = torch.from_numpy(rho_host).to(dev)
+    phi = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    acc = torch.empty((3, n, n, n), dtype=torch.float32, device=dev)
+    l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    plan = B.Plan(n, L, p)
+    if tc:
+        plan.set_precision(prec)
     with ClockSampler(dev.index) as clk:
-        for _ in range(args.steps):
-            l2_flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            plan.solve(rho, phi, acc)
-            e1.record(stream)
-            e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
-            stage.append(B.fmm_plan_stage_times(plan.handle))
-        torch.cuda.synchronize()
-        barrier()
-    wall = time.perf_counter() - wall0
-    B.fmm_plan_set_timing(plan.handle, False)
+        step_ms, stage, wall = _time_solves(B, plan, rho, phi, acc, args.steps, args.warmup, l2_flush, stream,
+                                            barrier)
     ms = statistics.mean(step_ms)
     if ws > 1:
         import torch.distributed as dist
@@ -232,6 +277,8 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = ws * n ** 3 / (ms / 1000.0)
+    result_phi = phi.cpu().numpy() if (rank == 0 and ws == 1 and not args.no_cpu_baseline) else None
+    result_acc = acc.cpu().numpy() if result_phi is not None else None
 
     # per-stage means over the timed steps
     nslot = len(stage[0])
@@ -240,29 +287,48 @@ def run_ours(args):
     stage_ms = {names[i]: st[i] for i in range(6)}
     for lev in range(2, L + 1):
         stage_ms[f"m2l_level{lev}"] = st[B.FMM_TIME_M2L_LEVEL0 + lev]
+
+    # the plain FP32 form on the same field, same run (the comparison the metric names)
+    plain = None
+    if tc and not args.no_plain:
+        pplan = B.Plan(n, L, p)
+        pms, pstage, _ = _time_solves(B, pplan, rho, phi, acc, max(1, min(args.steps, 3)), max(1, min(args.warmup, 2)),
+                                      l2_flush, stream, barrier)
+        pm_ = statistics.mean(pms)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([pm_], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            pm_ = float(t.item())
+        plain = {"value": ws * n ** 3 / (pm_ / 1000.0), "ms_per_step": pm_,
+                 "m2l_ms": statistics.mean(s[B.FMM_TIME_M2L] for s in pstage),
+                 "p2p_ms": statistics.mean(s[B.FMM_TIME_P2P] for s in pstage)}
+        pplan.close()
+
     peaks, src = _peaks()
+    fp32_peak = SM_COUNT * FP32_FMA_PER_SM_PER_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
     dominant = max(names, key=lambda k: stage_ms[k])
-    if dominant == "p2p_l2p":
-        clk_mhz = SM_MAX_MHZ
-        peak = SM_COUNT * FP32_FMA_PER_SM_PER_CLK * 2 * clk_mhz * 1e6 / 1e12
-        ach = p2p_flops(n, L) / (stage_ms["p2p_l2p"] / 1000.0) / 1e12
-        roof = {"kernel": "k_p2p (fused L2P + near-zone sum)", "bound": "alu", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "peak_source": f"152 SMs x 128 FP32 FMA/clk x 2 flop x {clk_mhz:.0f} MHz (derived)"}
-    else:
-        ach = m2l_flops(L, p) / (stage_ms["m2l"] / 1000.0) / 1e12
-        if prec == B.FMM_PREC_FP32:
-            peak = SM_COUNT * FP32_FMA_PER_SM_PER_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
-            roof = {"kernel": "k_m2l_fp32", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None,
-                    "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz (derived)"}
-        else:
-            peak = peaks.get("bf16_tflops_sustained", 1700.0)
-            roof = {"kernel": "m2l tensor", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None, "peak_source": f"bf16_tflops_sustained ({src})"}
+    p2p_ach = p2p_flops(n, L) / (stage_ms["p2p_l2p"] / 1000.0) / 1e12
+    roof_p2p = {"kernel": "k_p2p (fused L2P + near-zone sum)", "bound": "alu", "achieved": p2p_ach,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": p2p_ach / fp32_peak,
+                "traffic": P2P_TRAFFIC.get((n, L, p)),
+                "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz (derived)"}
+    tc_levels = [lev for lev in range(4, L + 1)] if tc else []
+    roof_m2l = None
+    if tc_levels:
+        tc_ms = sum(stage_ms[f"m2l_level{lev}"] for lev in tc_levels)
+        alg = sum(2.0 * 4 * p ** 3 * p ** 3 * 189 * 8 ** lev for lev in tc_levels)
+        ach = alg / (tc_ms / 1000.0) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        roof_m2l = {"kernel": "k_m2l_tc (levels " + ",".join(map(str, tc_levels)) + ")", "bound": "tensor",
+                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "executed_tflops": ach * (3 if prec == B.FMM_PREC_BF16X3 else 1),
+                    "peak_source": f"bf16_tflops_sustained ({src}); achieved counts the algorithmic contraction, "
+                                   "bf16x3 executes 3 MMAs per product"}
+    roof = roof_p2p if (dominant == "p2p_l2p" or roof_m2l is None) else roof_m2l
 
     # end to end through the public host-buffer entry point
-    hin = torch.from_numpy(workload_density(n, rank)).pin_memory()
+    hin = torch.from_numpy(rho_host).pin_memory()
     hphi = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
     hacc = torch.empty((3, n, n, n), dtype=torch.float32).pin_memory()
     B.fmm_solve_host(plan.handle, hin, hphi, hacc, stream)
@@ -271,6 +337,7 @@ def run_ours(args):
     for _ in range(e2e_steps):
         B.fmm_solve_host(plan.handle, hin, hphi, hacc, stream)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    plan.close()
 
     if rank != 0:
         if ws > 1:
@@ -281,25 +348,30 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if prec == B.FMM_PREC_FP32 else args.precision,
+        "vs_baseline": None, "dtype": "f32" if not tc else ("bf16x3" if prec == B.FMM_PREC_BF16X3 else "bf16"),
         "data": "synthetic",
         "config": {"workload": f"{n}^3 lognormal sigma=0.5 (seeded), order p={p}, L={L} (S={n >> L}), "
-                               f"M2L {args.precision}",
+                               f"M2L levels>=4 {args.precision}, levels 2-3 FP32 split-table",
                    "N": n, "L": L, "order": p, "precision": args.precision,
                    "l2_flush": "256 MB buffer written between timed steps",
                    "parallelism": f"replicas x{ws}"},
         "stage_ms": stage_ms,
         "wall_s": wall,
         "roofline": roof,
+        "roofline_p2p": roof_p2p,
+        "roofline_m2l": roof_m2l,
         "e2e": {"value": ws * n ** 3 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * n ** 3,
                 "d2h_bytes_per_step": 16 * n ** 3},
-        "gpu_launches": launches_per_solve * args.steps,
+        "gpu_launches": launches_per_solve(L, tc) * args.steps,
         "clocks": clocks,
     }
+    if plain is not None:
+        line["plain_fp32"] = plain
+        line["speedup_vs_plain_fp32"] = plain["ms_per_step"] / ms
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        line["accuracy"] = accuracy_vs_pm(rho_host, result_phi, result_acc)
     print(json.dumps(line), flush=True)
-    plan.close()
     return 0
 
 
@@ -312,8 +384,9 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--L", type=int, default=5)
     ap.add_argument("--p", type=int, default=6)
-    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x3"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x3"], default="bf16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 form")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
