@@ -170,6 +170,31 @@ const char* fmm_error_string(int code);
 int fmm_plan_copy_stage(fmm_plan* plan, int stage, int level, float* dst,
                         size_t count, void* stream);
 
+/* ---- allocation-free entry point ----------------------------------------- */
+
+/* Mean of a device float array, without any allocation by the library.  The
+ * paper has no counterpart: this is a service for callers that cannot let a
+ * library call cudaMalloc / cudaFree (embedders whose own allocator owns all
+ * device memory; host loops that must not take the device-wide
+ * synchronisation those calls may cause).  It computes the same FP64 mean of
+ * the density as the first step of fmm_solve.
+ *   density  device, `count` floats, read only.
+ *   count    1 .. 134217728 (= 512^3); larger counts return FMM_ERR_ARG.
+ *   mean     device, one double, written.
+ *   stream   cudaStream_t as void* (NULL = legacy default stream); the call
+ *            only enqueues work.
+ * Scratch: a file-scope static device array of 16384 doubles (128 KB) that
+ * every GPU which loads this library holds until the process exits.  Every
+ * call on a device shares it and it keeps the last call's contents (each call
+ * overwrites the slots it reads), so calls whose work overlaps on the GPU
+ * (different streams, or different host threads on one device) race and must
+ * be serialised by the caller.  The first call on each device looks up the
+ * array's device address with that device current (a one-time set-up); make
+ * that first call before any stream capture.
+ * Returns FMM_OK, FMM_ERR_ARG (NULL pointers, count 0 or above the maximum),
+ * FMM_ERR_UNSUPPORTED (device ordinal >= 64) or FMM_ERR_CUDA. */
+int fmm_mean_density_noalloc(const float* density, size_t count, double* mean, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

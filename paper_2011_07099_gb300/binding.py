@@ -49,6 +49,7 @@ SIGNATURES = {
     "fmm_plan_set_m2l_group": (_I, [_VP, _I]),
     "fmm_plan_set_timeout_ms": (_I, [_VP, _I]),
     "fmm_plan_inject_fault": (_I, [_VP, _I]),
+    "fmm_mean_density_noalloc": (_I, [_FP, _SZ, _FP, _VP]),
     "fmm_plan_stage_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), _I]),
 }
 

@@ -123,6 +123,8 @@ bool dev_alloc(T** ptr, size_t count) {
 
 }  // namespace
 
+int fmm::set_last_error(int code) { return set_err(code); }
+
 extern "C" {
 
 int fmm_last_error(void) { return g_last_error; }

@@ -9,6 +9,9 @@
 
 namespace fmm {
 
+// Records `code` as the calling host thread's last error and returns it.
+int set_last_error(int code);
+
 constexpr int kMaxLevel = 8;
 constexpr int kMaxOrder = 8;
 constexpr int kFields = 4;          // Phi, g_x, g_y, g_z
