@@ -152,6 +152,52 @@ int fmm_plan_set_timing(fmm_plan* plan, int enable);
  * that solve to finish.  FMM_ERR_ARG if timing was never enabled. */
 int fmm_plan_stage_times(fmm_plan* plan, float* ms, int n);
 
+/* ---- learned table correction ------------------------------------------- */
+/* Sec. 4 proposes parameterising the optimal Green's function G_* by many
+ * parameters instead of the analytic G_S1.  Here a small MLP
+ * (5 -> 64 -> 64 -> 64 -> 1, GELU) adds a learned correction to every M2L
+ * table entry; the near zone keeps the exact G_S1 (it must match PM).
+ * Inputs: the entry's offset in gridlet units (absolute values, sorted so
+ * the cube symmetry holds), the level and the field class (G or a gradient
+ * component, the latter times the sign of its own offset component); the
+ * output is scaled by the entry's natural size at that level.  Parameter
+ * layout (FP32): W1[64][5] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[64]
+ * b4[1], FMM_MLP_PARAMS floats. */
+#define FMM_MLP_PARAMS 8769
+#define FMM_INFER_BF16 0      /* weights and activations rounded to BF16, FP32 accumulate */
+#define FMM_INFER_FP32 1
+
+/* Set (weights = device or host pointer to FMM_MLP_PARAMS floats, copied) or
+ * clear (weights = NULL) the correction and re-tabulate every M2L table form
+ * (synchronous).  FMM_ERR_ARG if n != FMM_MLP_PARAMS. */
+int fmm_plan_set_correction(fmm_plan* plan, const float* weights, size_t n);
+
+/* Inference arithmetic of the correction at the next fmm_plan_set_correction:
+ * FMM_INFER_BF16 (default) or FMM_INFER_FP32 (used for training). */
+int fmm_plan_set_correction_inference(fmm_plan* plan, int mode);
+
+/* One training field: solve `density` (device, N^3) with the current
+ * correction, compare with the target solution (device, N^3 potential and
+ * 3 N^3 acceleration), and ADD to `grad` (device, FMM_MLP_PARAMS floats) the
+ * gradient of J = w_phi |Phi - Phi*|^2 + w_g |g - g*|^2 with respect to the
+ * correction's parameters, and J itself to `loss` (device, 1 float).  The
+ * gradient runs through the adjoint of L2P and L2L, the table gradient of
+ * eq. fmm2 and the MLP's backward pass, all on the GPU.  Requires a
+ * correction to be set (FMM_ERR_ARG otherwise).  Enqueued on `stream`. */
+int fmm_correction_grad(fmm_plan* plan, const float* density, const float* target_phi, const float* target_acc,
+                        float w_phi, float w_g, float* grad, float* loss, void* stream);
+
+/* One Adam update of n parameters (device arrays; m, v are the moment
+ * estimates, step >= 1 the update count for bias correction). */
+int fmm_adam_step(float* weights, const float* grad, float* m, float* v, size_t n, int step, float lr, float beta1,
+                  float beta2, float eps, void* stream);
+
+/* G_S1 and -grad G_S1 at the periodic mesh offsets d/N, d in [0, N)^3, with
+ * the cell self term at d = 0: `out` (device) = 4 planes of N^3 floats in
+ * [z][y][x] order (G, -dG/dx, -dG/dy, -dG/dz).  The kernel of the PM solution
+ * with the same Green's function (Sec. 3 eq. pmconv). */
+int fmm_mesh_green(int N, float* out, void* stream);
+
 /* ---- errors --------------------------------------------------------- */
 int fmm_last_error(void);
 const char* fmm_error_string(int code);

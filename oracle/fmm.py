@@ -220,10 +220,12 @@ def p2p_kernel(N, S, off_zyx):
 
 
 # ------------------------------------------------------------- far field
-def m2l(level, p, M, targets):
+def m2l(level, p, M, targets, correction=None):
     """a5/a6: eq. fmm2 for the given target nodes ((k,3) int array, (z,y,x)).
     Returns (k, 4, p^3): Phi and g = -grad Phi at the target gridlet points
-    from the multipoles of the target's interaction zone."""
+    from the multipoles of the target's interaction zone.  ``correction``,
+    if given, is a function (level, p, offset) -> (4, p^3, p^3) added to the
+    translation matrices (the learned table correction)."""
     n = 2 ** level
     targets = np.asarray(targets, dtype=np.int64).reshape(-1, 3)
     out = np.zeros((targets.shape[0], FIELDS, p ** 3))
@@ -237,6 +239,8 @@ def m2l(level, p, M, targets):
                 T = targets[sel]
                 for off in interaction_offsets(level, (cz, cy, cx)):
                     K = m2l_kernel(level, p, off)
+                    if correction is not None:
+                        K = K + correction(level, p, off)
                     src = (T - np.array(off)) % n
                     Ms = M[src[:, 0], src[:, 1], src[:, 2]]
                     out[sel] += (Ms @ K.reshape(FIELDS * p ** 3, p ** 3).T).reshape(-1, FIELDS, p ** 3)
@@ -255,13 +259,13 @@ def all_nodes(level):
     return g
 
 
-def downward(M, L, p):
+def downward(M, L, p, correction=None):
     """Local fields for every node: M2L at each level plus L2L from the parent.
     Returns {level: (n,n,n,4,p^3)}."""
     F = {}
     for lev in range(2, L + 1):
         n = 2 ** lev
-        loc = m2l(lev, p, M[lev], all_nodes(lev)).reshape(n, n, n, FIELDS, p ** 3)
+        loc = m2l(lev, p, M[lev], all_nodes(lev), correction).reshape(n, n, n, FIELDS, p ** 3)
         if lev > 2:
             for cz in range(2):
                 for cy in range(2):
@@ -297,8 +301,9 @@ def l2p_matrix(S, p):
 
 
 # ---------------------------------------------------------------- solve
-def solve(rho, L, p):
-    """Full FMM solve.  Returns (phi (N,N,N), g (3,N,N,N))."""
+def solve(rho, L, p, correction=None):
+    """Full FMM solve.  Returns (phi (N,N,N), g (3,N,N,N)).  ``correction`` as
+    in ``m2l``."""
     rho = np.asarray(rho, dtype=np.float64)
     N = rho.shape[0]
     n = 2 ** L
@@ -307,7 +312,7 @@ def solve(rho, L, p):
         raise ValueError("need N divisible by 2^L and L >= 2")
     m = masses(rho)
     M = upward(m, L, p)
-    F = downward(M, L, p)
+    F = downward(M, L, p, correction)
     far = F[L] @ l2p_matrix(S, p).T                            # (n,n,n,4,S^3)
     near = p2p(m, L, all_nodes(L)).reshape(n, n, n, FIELDS, S ** 3)
     tot = np.moveaxis(far + near, 3, 0)                         # (4,n,n,n,S^3)

@@ -24,6 +24,10 @@ FMM_PREC_FP32 = 0
 FMM_PREC_BF16 = 1
 FMM_PREC_BF16X3 = 2
 
+FMM_MLP_PARAMS = 8769
+FMM_INFER_BF16 = 0
+FMM_INFER_FP32 = 1
+
 FMM_FAULT_NONE = 0
 FMM_FAULT_TC_STALL = 1
 
@@ -50,6 +54,12 @@ SIGNATURES = {
     "fmm_plan_set_timeout_ms": (_I, [_VP, _I]),
     "fmm_plan_inject_fault": (_I, [_VP, _I]),
     "fmm_mean_density_noalloc": (_I, [_FP, _SZ, _FP, _VP]),
+    "fmm_plan_set_correction": (_I, [_VP, _FP, _SZ]),
+    "fmm_plan_set_correction_inference": (_I, [_VP, _I]),
+    "fmm_correction_grad": (_I, [_VP, _FP, _FP, _FP, ctypes.c_float, ctypes.c_float, _FP, _FP, _VP]),
+    "fmm_adam_step": (_I, [_FP, _FP, _FP, _FP, _SZ, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                           ctypes.c_float, _VP]),
+    "fmm_mesh_green": (_I, [_I, _FP, _VP]),
     "fmm_plan_stage_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), _I]),
 }
 
@@ -141,6 +151,34 @@ def fmm_plan_set_timeout_ms(plan, ms):
 
 def fmm_plan_inject_fault(plan, kind):
     _check(lib().fmm_plan_inject_fault(plan, int(kind)), "fmm_plan_inject_fault")
+
+
+def fmm_plan_set_correction(plan, weights):
+    """weights: torch tensor (device or host) of FMM_MLP_PARAMS floats, or None."""
+    if weights is None:
+        _check(lib().fmm_plan_set_correction(plan, None, 0), "fmm_plan_set_correction")
+    else:
+        _check(lib().fmm_plan_set_correction(plan, weights.data_ptr(), weights.numel()), "fmm_plan_set_correction")
+
+
+def fmm_plan_set_correction_inference(plan, mode):
+    _check(lib().fmm_plan_set_correction_inference(plan, int(mode)), "fmm_plan_set_correction_inference")
+
+
+def fmm_correction_grad(plan, density, target_phi, target_acc, w_phi, w_g, grad, loss, stream=None):
+    _check(lib().fmm_correction_grad(plan, density.data_ptr(), target_phi.data_ptr(), target_acc.data_ptr(),
+                                     float(w_phi), float(w_g), grad.data_ptr(), loss.data_ptr(),
+                                     _stream_of(density, stream)), "fmm_correction_grad")
+
+
+def fmm_adam_step(weights, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().fmm_adam_step(weights.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), weights.numel(),
+                               int(step), float(lr), float(beta1), float(beta2), float(eps),
+                               _stream_of(weights, stream)), "fmm_adam_step")
+
+
+def fmm_mesh_green(N, out, stream=None):
+    _check(lib().fmm_mesh_green(int(N), out.data_ptr(), _stream_of(out, stream)), "fmm_mesh_green")
 
 
 def fmm_plan_check(plan):

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "fmm_internal.cuh"
+#include "mlp.cuh"
 
 using fmm::Plan;
 
@@ -99,6 +100,12 @@ void free_plan(Plan* P) {
   }
   cudaFree(P->near_tab);
   cudaFree(P->d_err);
+  cudaFree(P->corr_w);
+  cudaFree(P->train_out);
+  cudaFree(P->lam_cells);
+  cudaFree(P->dT_all);
+  cudaFree(P->grad_partials);
+  for (int l = 0; l <= fmm::kMaxLevel; ++l) cudaFree(P->lam[l]);
   for (int l = 0; l <= fmm::kMaxLevel; ++l) {
     cudaFree(P->tab_bf[l]);
     cudaFree(P->Mbf_hi[l]);
@@ -229,7 +236,7 @@ fmm_plan* fmm_plan_create(int N, int L, int order) {
     return nullptr;
   }
   if (fmm::setup_upward(*P) != cudaSuccess || fmm::setup_m2l_fp32(*P) != cudaSuccess ||
-      fmm::setup_m2l_tc(*P) != cudaSuccess ||
+      fmm::setup_m2l_tc(*P) != cudaSuccess || fmm::setup_learn() != cudaSuccess ||
       fmm::setup_downward(*P) != cudaSuccess || fmm::setup_p2p(*P) != cudaSuccess ||
       fmm::launch_tables(*P, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
     free_plan(P);
@@ -304,6 +311,76 @@ int fmm_plan_inject_fault(fmm_plan* plan, int kind) {
 int fmm_plan_set_m2l_group(fmm_plan* plan, int offsets_per_partial) {
   if (!plan || offsets_per_partial < 1 || offsets_per_partial > fmm::kMaxOffsets) return set_err(FMM_ERR_ARG);
   reinterpret_cast<Plan*>(plan)->tc_group = offsets_per_partial;
+  return set_err(FMM_OK);
+}
+
+int fmm_plan_set_correction_inference(fmm_plan* plan, int mode) {
+  if (!plan || (mode != FMM_INFER_BF16 && mode != FMM_INFER_FP32)) return set_err(FMM_ERR_ARG);
+  reinterpret_cast<Plan*>(plan)->corr_fp32 = mode == FMM_INFER_FP32 ? 1 : 0;
+  return set_err(FMM_OK);
+}
+
+int fmm_plan_set_correction(fmm_plan* plan, const float* weights, size_t n) {
+  if (!plan) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  if (weights) {
+    if (n != (size_t)fmm::mlp::kParams) return set_err(FMM_ERR_ARG);
+    if (!P.corr_w && !dev_alloc(&P.corr_w, (size_t)fmm::mlp::kParams)) return set_err(FMM_ERR_ALLOC);
+    FMM_CUDA_TRY(cudaMemcpy(P.corr_w, weights, n * sizeof(float), cudaMemcpyDefault));
+    P.has_corr = 1;
+  } else {
+    P.has_corr = 0;
+  }
+  // re-tabulate every table form from G_S1 (+ the correction)
+  FMM_CUDA_TRY(fmm::launch_tables(P, 0));
+  if (P.tc_ready) {
+    for (int l = fmm::kTcMinLevel; l <= P.L; ++l) {
+      FMM_CUDA_TRY(fmm::launch_tab_bf16(P, l, 0));
+      FMM_CUDA_TRY(fmm::launch_build_a(P, l, 0));
+    }
+  }
+  FMM_CUDA_TRY(cudaDeviceSynchronize());
+  return set_err(FMM_OK);
+}
+
+int fmm_correction_grad(fmm_plan* plan, const float* density, const float* target_phi, const float* target_acc,
+                        float w_phi, float w_g, float* grad, float* loss, void* stream) {
+  if (!plan || !density || !target_phi || !target_acc || !grad || !loss) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  if (!P.has_corr) return set_err(FMM_ERR_ARG);
+  const size_t n3 = (size_t)P.N * P.N * P.N;
+  const size_t p3 = (size_t)P.p * P.p * P.p, E = 8 * P.p - 1;
+  if (!P.train_out) {
+    bool ok = dev_alloc(&P.train_out, 4 * n3) && dev_alloc(&P.lam_cells, 4 * n3) &&
+              dev_alloc(&P.dT_all, (size_t)(P.L - 1) * E * E * E * 4) &&
+              dev_alloc(&P.grad_partials, (size_t)fmm::mlp_backward_blocks(P) * fmm::mlp::kParams);
+    for (int l = 2; l <= P.L && ok; ++l) ok = dev_alloc(&P.lam[l], ((size_t)1 << (3 * l)) * 4 * p3);
+    if (!ok) return set_err(FMM_ERR_ALLOC);
+    for (int l = 2; l <= P.L; ++l) P.dT[l] = P.dT_all + (size_t)(l - 2) * E * E * E * 4;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int rc = fmm_solve(plan, density, P.train_out, P.train_out + n3, stream);
+  if (rc != FMM_OK) return rc;
+  FMM_CUDA_TRY(fmm::launch_residual(P.train_out, P.train_out + n3, target_phi, target_acc, n3, w_phi, w_g, P.lam_cells,
+                                    loss, P.num_sms, s));
+  FMM_CUDA_TRY(fmm::launch_adjoint_and_table_grad(P, P.lam_cells, s));
+  FMM_CUDA_TRY(fmm::launch_mlp_backward(P, P.corr_w, grad, s));
+  return set_err(FMM_OK);
+}
+
+int fmm_adam_step(float* w, const float* g, float* m, float* v, size_t n, int step, float lr, float beta1, float beta2,
+                  float eps, void* stream) {
+  if (!w || !g || !m || !v || n == 0 || step < 1) return set_err(FMM_ERR_ARG);
+  FMM_CUDA_TRY(fmm::launch_adam(w, g, m, v, n, step, lr, beta1, beta2, eps, reinterpret_cast<cudaStream_t>(stream)));
+  return set_err(FMM_OK);
+}
+
+int fmm_mesh_green(int N, float* out, void* stream) {
+  if (N < 2 || !out) return set_err(FMM_ERR_ARG);
+  int dev = 0, sms = 0;
+  FMM_CUDA_TRY(cudaGetDevice(&dev));
+  FMM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  FMM_CUDA_TRY(fmm::launch_mesh_green(N, out, sms, reinterpret_cast<cudaStream_t>(stream)));
   return set_err(FMM_OK);
 }
 

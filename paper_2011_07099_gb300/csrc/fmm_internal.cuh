@@ -80,6 +80,16 @@ struct Plan {
   void* Mbf_lo[kMaxLevel + 1] = {};        // unused (kept null)
   void* Apre[kMaxLevel + 1] = {};          // precomputed split translation tiles per offset slot
   int tc_group = 2;                        // offsets accumulated per TMEM partial before promotion
+  // learned table correction (MLP weights) and its training buffers
+  float* corr_w = nullptr;                 // mlp::kParams weights (device) or unset
+  int has_corr = 0;
+  int corr_fp32 = 0;                       // 0: BF16 inference (default), 1: FP32
+  float* train_out = nullptr;              // 4 N^3: the solve's outputs during training
+  float* lam_cells = nullptr;              // 4 N^3: cell residual adjoint
+  float* lam[kMaxLevel + 1] = {};          // adjoint of the local fields, 8^l x 4 x p^3
+  float* dT_all = nullptr;                 // table gradients, levels 2..L, (8p-1)^3 x 4 each
+  float* dT[kMaxLevel + 1] = {};
+  float* grad_partials = nullptr;          // per-block MLP gradient partials
   uint64_t wait_ns = 2000000000ull;        // limit of every bounded device-side wait
   int inject_stall = 0;                    // test hook: tensor-core MMA issuer stalls
   int tc_ready = 0;
@@ -114,6 +124,15 @@ cudaError_t launch_m2l_fp32(Plan& P, int level, cudaStream_t s);  // writes F[le
 cudaError_t launch_l2l(Plan& P, int level, cudaStream_t s);       // F[level] -> F[level+1] (adds)
 cudaError_t launch_p2p(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s);
 cudaError_t setup_m2l_tc(const Plan& P);
+cudaError_t setup_learn();
+cudaError_t launch_residual(const float* phi, const float* acc, const float* tphi, const float* tacc, size_t n3,
+                            float w_phi, float w_g, float* lam, float* loss, int sms, cudaStream_t s);
+cudaError_t launch_adjoint_and_table_grad(Plan& P, const float* lam_cells, cudaStream_t s);
+cudaError_t launch_mlp_backward(Plan& P, const float* w, float* grad, cudaStream_t s);
+int mlp_backward_blocks(const Plan& P);
+cudaError_t launch_adam(float* w, const float* g, float* m, float* v, size_t n, int step, float lr, float b1, float b2,
+                        float eps, cudaStream_t s);
+cudaError_t launch_mesh_green(int N, float* out, int sms, cudaStream_t s);
 cudaError_t launch_tab_bf16(Plan& P, int level, cudaStream_t s);
 cudaError_t launch_split_bf16(Plan& P, int level, cudaStream_t s);
 cudaError_t launch_m2l_tc(Plan& P, int level, int mode, cudaStream_t s);

@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 
 #include "fmm_internal.cuh"
+#include "mlp.cuh"
 
 namespace fmm {
 namespace {
@@ -37,11 +38,25 @@ __device__ inline void gs1(double x, double y, double z, double out[4]) {
   out[3] = c * hz * dxi_s1(z);
 }
 
+// Learned correction of one table entry (all four fields), if weights are set.
+__device__ inline void add_correction(double v[4], int ix, int iy, int iz, int level, int p, const float* mlp, int fp32) {
+  if (!mlp || !(ix | iy | iz)) return;
+  for (int f = 0; f < 4; ++f) {
+    float x[mlp::kIn], sign;
+    double scale;
+    mlp::features(ix, iy, iz, f, level, p, x, sign, scale);
+    if (sign == 0.f) continue;
+    const float o = fp32 ? mlp::forward<false>(mlp, x) : mlp::forward<true>(mlp, x);
+    v[f] += (double)o * (double)sign * scale;
+  }
+}
+
 // M2L table of level l: n in [-(4p-1), 4p-1]^3 at spacing dx_l = 1/(2^l p)
 // (Sec. 3: gridlet spacing of a level-l node; the (4 N_g)^D samples of Sec. 4
 // folded over the sign of each component).  Entry n = 0 is never used by M2L
 // (the interaction zone excludes near nodes) and is stored as 0.
-__global__ void k_tab_m2l(float4* __restrict__ out, float* __restrict__ lo, int p, int level) {
+__global__ void k_tab_m2l(float4* __restrict__ out, float* __restrict__ lo, int p, int level, const float* mlp,
+                          int fp32) {
   const int hw = 4 * p - 1, E = 8 * p - 1;
   const long total = (long)E * E * E;
   const double dx = 1.0 / ((double)(1 << level) * p);
@@ -49,6 +64,7 @@ __global__ void k_tab_m2l(float4* __restrict__ out, float* __restrict__ lo, int 
     const int ix = (int)(i % E) - hw, iy = (int)((i / E) % E) - hw, iz = (int)(i / ((long)E * E)) - hw;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (ix | iy | iz) gs1(ix * dx, iy * dx, iz * dx, v);
+    add_correction(v, ix, iy, iz, level, p, mlp, fp32);
     out[i] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
     if (lo) lo[i] = (float)(v[0] - (double)(float)v[0]);
   }
@@ -79,7 +95,7 @@ __global__ void k_tab_near(float4* __restrict__ out, int S, int N) {
 // The same level table split into BF16 hi + lo per field for the tensor-core
 // M2L: each uint32 holds hi in its low half and lo = bf16(v - hi) in its high
 // half, the four fields in the four words of a uint4.
-__global__ void k_tab_bf16(uint4* __restrict__ out, int p, int level) {
+__global__ void k_tab_bf16(uint4* __restrict__ out, int p, int level, const float* mlp, int fp32) {
   const int hw = 4 * p - 1, E = 8 * p - 1;
   const long total = (long)E * E * E;
   const double dx = 1.0 / ((double)(1 << level) * p);
@@ -87,6 +103,7 @@ __global__ void k_tab_bf16(uint4* __restrict__ out, int p, int level) {
     const int ix = (int)(i % E) - hw, iy = (int)((i / E) % E) - hw, iz = (int)(i / ((long)E * E)) - hw;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (ix | iy | iz) gs1(ix * dx, iy * dx, iz * dx, v);
+    add_correction(v, ix, iy, iz, level, p, mlp, fp32);
     uint32_t w[4];
     for (int f = 0; f < 4; ++f) {
       const __nv_bfloat16 h = __double2bfloat16(v[f]);
@@ -100,13 +117,15 @@ __global__ void k_tab_bf16(uint4* __restrict__ out, int p, int level) {
 }  // namespace
 
 cudaError_t launch_tab_bf16(Plan& P, int level, cudaStream_t s) {
-  k_tab_bf16<<<4 * P.num_sms, 256, 0, s>>>(P.tab_bf[level], P.p, level);
+  k_tab_bf16<<<4 * P.num_sms, 256, 0, s>>>(P.tab_bf[level], P.p, level, P.has_corr ? P.corr_w : nullptr,
+                                           P.corr_fp32);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tables(Plan& P, cudaStream_t s) {
   for (int l = 2; l <= P.L; ++l) {
-    k_tab_m2l<<<4 * P.num_sms, 256, 0, s>>>(P.tab[l], P.tab_lo[l], P.p, l);
+    k_tab_m2l<<<4 * P.num_sms, 256, 0, s>>>(P.tab[l], P.tab_lo[l], P.p, l, P.has_corr ? P.corr_w : nullptr,
+                                            P.corr_fp32);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
