@@ -17,6 +17,8 @@ time.  ``--impl reference`` times the FP64 CPU oracle instead (rank 0 only).
 """
 import argparse
 import json
+
+import numpy as np
 import os
 import statistics
 import subprocess
@@ -375,6 +377,57 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """The batching workload: 64 independent periodic fields with N drawn from
+    {32, 48, 64, 96, 128}, order 4 or 6, lognormal sigma in [0.3, 1.5]
+    (seeded), leaf levels autotuned, solved as one CUDA-graph launch."""
+    import torch
+    from paper_2011_07099_gb300 import binding as B, build, inputs
+    torch.cuda.set_device(0)
+    build.build()
+    rng = np.random.Generator(np.random.PCG64(2000))
+    nf = args.fields
+    Ns = [int(x) for x in rng.choice([32, 48, 64, 96, 128], nf)]
+    ps = [int(x) for x in rng.choice([4, 6], nf)]
+    sig = rng.uniform(0.3, 1.5, nf)
+    os.environ.setdefault("FMM_AUTOTUNE_CACHE", os.path.join(ROOT, "gpurun_out", "autotune.jsonl"))
+    t0 = time.perf_counter()
+    batch = B.Batch(Ns, [0] * nf, ps, precision=B.FMM_PREC_BF16X3)
+    tune_s = time.perf_counter() - t0
+    d = [torch.from_numpy(inputs.lognormal(n, sigma=float(s_), seed=2000 + i)).cuda() for i, (n, s_) in
+         enumerate(zip(Ns, sig))]
+    pots = [torch.empty((n, n, n), device="cuda") for n in Ns]
+    accs = [torch.empty((3, n, n, n), device="cuda") for n in Ns]
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        batch.solve(d, pots, accs)
+    torch.cuda.synchronize()
+    l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    times = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            l2_flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            batch.solve(d, pots, accs)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    batch.check()
+    ms = statistics.mean(times)
+    cells = sum(n ** 3 for n in Ns)
+    line = {"metric": "FMM cells/s, batch of 64 uneven periodic fields (one graph launch)", "value": cells / (ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+            "config": {"workload": f"{nf} fields, N in {{32,48,64,96,128}}, p in {{4,6}}, lognormal sigma U[0.3,1.5]",
+                       "cells": cells, "levels": batch.levels, "N": Ns, "order": ps, "autotune_s": tune_s},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    batch.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -387,9 +440,13 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x3"], default="bf16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 form")
+    ap.add_argument("--workload", choices=["headline", "batch"], default="headline")
+    ap.add_argument("--fields", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

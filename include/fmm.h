@@ -56,7 +56,7 @@ typedef struct fmm_plan fmm_plan;
 /* ---- plan lifecycle -------------------------------------------------- */
 
 /* Create a plan for an N^3 periodic mesh, leaf level L and gridlet order.
- *   N     mesh cells per dimension; N = S * 2^L with S in {1, 2, 4, 8}.
+ *   N     mesh cells per dimension; N = S * 2^L with S in {1, 2, 3, 4, 6, 8}.
  *   L     leaf level, 2 <= L <= 8 (L = 2 is the two-level special case of
  *         Sec. 3, exact when order == S; the general case is L >= 3, Sec. 2).
  *   order gridlet points per dimension (N_g), 1 <= order <= 8.
@@ -151,6 +151,45 @@ int fmm_plan_set_timing(fmm_plan* plan, int enable);
  * FMM_TIME_*; writes min(n, FMM_TIME_SLOTS) floats (unused slots 0).  Waits for
  * that solve to finish.  FMM_ERR_ARG if timing was never enabled. */
 int fmm_plan_stage_times(fmm_plan* plan, float* ms, int n);
+
+/* ---- batches of independent fields ------------------------------------------ */
+/* Many periodic fields of uneven size solved together: one plan per field,
+ * and every solve of the batch is a single CUDA-graph launch whose parallel
+ * branches are the fields (largest first, up to 8 concurrent branches). */
+typedef struct fmm_batch fmm_batch;
+
+/* nfields >= 1 fields with mesh sizes N[i], leaf levels L[i] and orders
+ * order[i] (each as in fmm_plan_create).  L[i] <= 0 picks the level with
+ * fmm_autotune_levels (mixed-precision M2L, cache file from the environment
+ * variable FMM_AUTOTUNE_CACHE if set).  Tensor-core precision is off until
+ * fmm_batch_set_precision.  NULL on error (fmm_last_error()). */
+fmm_batch* fmm_batch_create(int nfields, const int* N, const int* L, const int* order);
+
+/* M2L arithmetic of every field (FMM_PREC_*). */
+int fmm_batch_set_precision(fmm_batch* batch, int mode);
+
+/* The leaf level chosen for each field (nfields ints). */
+int fmm_batch_get_levels(const fmm_batch* batch, int* L);
+
+/* Solve every field: host arrays of nfields device pointers (each as in
+ * fmm_solve).  The first call with a given set of pointers captures the
+ * fields' kernels into one graph (later calls with the same pointers only
+ * launch it).  Enqueued on `stream`. */
+int fmm_batch_solve(fmm_batch* batch, const float* const* density, float* const* potential,
+                    float* const* accel, void* stream);
+
+/* fmm_plan_check over every field. */
+int fmm_batch_check(fmm_batch* batch);
+
+/* Release the batch (NULL allowed); synchronises the device first. */
+void fmm_batch_destroy(fmm_batch* batch);
+
+/* Autotuner: the leaf level L (S = N / 2^L in {2, 3, 4, 6, 8}, L >= 3 when
+ * possible) with the shortest solve of a synthetic N^3 field at this order
+ * and precision, timed with CUDA events (median of 3).  Results are cached
+ * per GPU model as JSON lines in `cache_path` (NULL: no cache).  Writes L and
+ * (if not NULL) its time in ms.  Allocates temporary device memory. */
+int fmm_autotune_levels(int N, int order, int precision, const char* cache_path, int* L_out, float* ms_out);
 
 /* ---- learned table correction ------------------------------------------- */
 /* Sec. 4 proposes parameterising the optimal Green's function G_* by many

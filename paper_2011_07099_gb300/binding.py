@@ -60,6 +60,13 @@ SIGNATURES = {
     "fmm_adam_step": (_I, [_FP, _FP, _FP, _FP, _SZ, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                            ctypes.c_float, _VP]),
     "fmm_mesh_green": (_I, [_I, _FP, _VP]),
+    "fmm_batch_create": (_VP, [_I, _VP, _VP, _VP]),
+    "fmm_batch_set_precision": (_I, [_VP, _I]),
+    "fmm_batch_get_levels": (_I, [_VP, _VP]),
+    "fmm_batch_solve": (_I, [_VP, _VP, _VP, _VP, _VP]),
+    "fmm_batch_check": (_I, [_VP]),
+    "fmm_batch_destroy": (None, [_VP]),
+    "fmm_autotune_levels": (_I, [_I, _I, _I, ctypes.c_char_p, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
     "fmm_plan_stage_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), _I]),
 }
 
@@ -193,6 +200,53 @@ def fmm_plan_stage_times(plan):
     buf = (ctypes.c_float * FMM_TIME_SLOTS)()
     _check(lib().fmm_plan_stage_times(plan, buf, FMM_TIME_SLOTS), "fmm_plan_stage_times")
     return list(buf)
+
+
+def fmm_autotune_levels(N, order, precision, cache_path=None):
+    L = ctypes.c_int()
+    ms = ctypes.c_float()
+    path = cache_path.encode() if cache_path else None
+    _check(lib().fmm_autotune_levels(int(N), int(order), int(precision), path, ctypes.byref(L), ctypes.byref(ms)),
+           "fmm_autotune_levels")
+    return L.value, ms.value
+
+
+class Batch:
+    """Owning wrapper of fmm_batch: fields of uneven size, one graph launch."""
+
+    def __init__(self, N, L, order, precision=FMM_PREC_FP32):
+        n = len(N)
+        arr = lambda v: (ctypes.c_int * n)(*[int(x) for x in v])
+        self.n = n
+        self.handle = lib().fmm_batch_create(n, arr(N), arr(L), arr(order))
+        if not self.handle:
+            raise FMMError(lib().fmm_last_error(), "fmm_batch_create")
+        if precision != FMM_PREC_FP32:
+            _check(lib().fmm_batch_set_precision(self.handle, int(precision)), "fmm_batch_set_precision")
+        lv = (ctypes.c_int * n)()
+        _check(lib().fmm_batch_get_levels(self.handle, lv), "fmm_batch_get_levels")
+        self.levels = list(lv)
+
+    def solve(self, densities, potentials, accels, stream=None):
+        n = self.n
+        ptrs = lambda ts: (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
+        s = _stream_of(densities[0], stream)
+        _check(lib().fmm_batch_solve(self.handle, ptrs(densities), ptrs(potentials), ptrs(accels), s),
+               "fmm_batch_solve")
+
+    def check(self):
+        _check(lib().fmm_batch_check(self.handle), "fmm_batch_check")
+
+    def close(self):
+        if self.handle:
+            lib().fmm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

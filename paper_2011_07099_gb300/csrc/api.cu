@@ -160,7 +160,7 @@ fmm_plan* fmm_plan_create(int N, int L, int order) {
     return nullptr;
   }
   const int S = N / n;
-  if (S != 1 && S != 2 && S != 4 && S != 8) {
+  if (S != 1 && S != 2 && S != 3 && S != 4 && S != 6 && S != 8) {
     set_err(FMM_ERR_ARG);
     return nullptr;
   }

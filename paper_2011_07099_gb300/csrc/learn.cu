@@ -406,6 +406,8 @@ int mlp_backward_blocks(const Plan& P) { return 2 * P.num_sms; }
 cudaError_t setup_learn() {
   cudaError_t e = cudaFuncSetAttribute(k_mlp_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_backward_smem());
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_table_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_adj_l2l, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_adj_l2p, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -197,7 +197,9 @@ cudaError_t setup_p2p(const Plan& P) {
   switch (P.S) {
     case 1: return setup_s<1>();
     case 2: return setup_s<2>();
+    case 3: return setup_s<3>();
     case 4: return setup_s<4>();
+    case 6: return setup_s<6>();
     case 8: return setup_s<8>();
     default: return cudaErrorInvalidValue;
   }
@@ -207,7 +209,9 @@ cudaError_t launch_p2p(Plan& P, const float* rho, float* phi, float* acc, cudaSt
   switch (P.S) {
     case 1: return launch_s<1>(P, rho, phi, acc, s);
     case 2: return launch_s<2>(P, rho, phi, acc, s);
+    case 3: return launch_s<3>(P, rho, phi, acc, s);
     case 4: return launch_s<4>(P, rho, phi, acc, s);
+    case 6: return launch_s<6>(P, rho, phi, acc, s);
     case 8: return launch_s<8>(P, rho, phi, acc, s);
     default: return cudaErrorInvalidValue;
   }

@@ -52,9 +52,9 @@ def test_error_strings(lib):
     assert binding.lib().fmm_error_string(99) == b"unknown error code"
 
 
-@pytest.mark.parametrize("args", [(32, 1, 2), (32, 9, 2), (30, 3, 2), (32, 3, 0), (32, 3, 9), (512, 3, 4), (0, 2, 2)])
+@pytest.mark.parametrize("args", [(32, 1, 2), (32, 9, 2), (30, 3, 2), (32, 3, 0), (32, 3, 9), (512, 3, 4), (0, 2, 2), (40, 3, 2), (80, 2, 3)])
 def test_plan_create_rejects_bad_shapes_before_touching_the_device(lib, args):
-    # sizes are validated on the host first: S must be 1, 2, 4 or 8, 2 <= L <= 8, 1 <= order <= 8
+    # sizes are validated on the host first: S in {1, 2, 3, 4, 6, 8}, 2 <= L <= 8, 1 <= order <= 8
     assert binding.lib().fmm_plan_create(*args) is None
     assert binding.lib().fmm_last_error() == binding.FMM_ERR_ARG
 
