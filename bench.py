@@ -428,6 +428,49 @@ def run_batch(args):
     return 0
 
 
+def run_full512(args):
+    """The full-scale workload: 512^3 (134M cells), order 8, L = 6 (S = 8),
+    density 1 + lognormal(sigma 1.5) plus 4096 Plummer clumps; the mixed form
+    (tensor-core bf16x3 M2L) against the plain FP32 form, errors against PM
+    with G_S1 (libfmm mesh Green's function + cuFFT)."""
+    import torch
+    from paper_2011_07099_gb300 import binding as B, build, inputs, learn
+    torch.cuda.set_device(0)
+    build.build()
+    n, L, p = 512, 6, 8
+    dev = torch.device("cuda", 0)
+    rho = inputs.config_density_torch(4, dev)
+    out = {}
+    l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    tphi, tacc = learn.pm_target(rho, n)
+    with ClockSampler(0) as clk:
+        for name, prec in (("mixed_bf16x3", B.FMM_PREC_BF16X3), ("plain_fp32", B.FMM_PREC_FP32)):
+            plan = B.Plan(n, L, p)
+            if prec:
+                plan.set_precision(prec)
+            phi = torch.empty((n, n, n), device=dev)
+            acc = torch.empty((3, n, n, n), device=dev)
+            ms, stage, _ = _time_solves(B, plan, rho, phi, acc, args.steps, max(1, args.warmup), l2_flush, stream,
+                                        lambda: None)
+            e_phi = float(((phi.double() - tphi.double()) ** 2).sum().sqrt() / (tphi.double() ** 2).sum().sqrt())
+            e_g = float(((acc.double() - tacc.double()) ** 2).sum().sqrt() / (tacc.double() ** 2).sum().sqrt())
+            st = [statistics.mean(s_[i] for s_ in stage) for i in range(len(stage[0]))]
+            out[name] = {"ms_per_step": statistics.mean(ms), "cells_per_s": n ** 3 / (statistics.mean(ms) / 1e3),
+                         "m2l_ms": st[B.FMM_TIME_M2L], "p2p_ms": st[B.FMM_TIME_P2P],
+                         "vs_pm_gs1": {"phi": e_phi, "g": e_g}}
+            plan.close()
+            del phi, acc
+    line = {"metric": "FMM cells/s at 512^3 p=8 (full scale)", "value": out["mixed_bf16x3"]["cells_per_s"],
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["mixed_bf16x3"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+            "config": {"workload": "512^3, p=8, L=6 (S=8), 1 + lognormal(sigma=1.5) + 4096 Plummer clumps",
+                       "forms": out}, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -440,13 +483,15 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x3"], default="bf16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 form")
-    ap.add_argument("--workload", choices=["headline", "batch"], default="headline")
+    ap.add_argument("--workload", choices=["headline", "batch", "full512"], default="headline")
     ap.add_argument("--fields", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "full512":
+        return run_full512(args)
     return run_ours(args)
 
 

@@ -3,7 +3,8 @@
 Shared by the tests, the bench and the oracle checks.  Holds none of the FMM's
 arithmetic: only the recipes that make density fields of the shapes the paper
 and its workloads use.  Every generator takes an explicit seed and returns a
-C-contiguous float32 array indexed [z][y][x] (x fastest).
+C-contiguous float32 array indexed [z][y][x] (x fastest); the ``*_torch``
+variants evaluate the same recipe on a torch device (for 512^3 fields).
 
 Recipes
 -------
@@ -41,10 +42,30 @@ def gaussian_field(n, rng, slope=-2.0):
     return g / s if s > 0 else g
 
 
-def lognormal(n, sigma=0.5, seed=0, amp=0.5, background=1.0):
+def gaussian_field_torch(n, rng, device, slope=-2.0):
+    """gaussian_field with the FFTs on a torch device (same white noise)."""
+    import torch
+    white = torch.from_numpy(rng.standard_normal((n, n, n))).to(device)
+    f = torch.fft.fftfreq(n, d=1.0 / n, device=device, dtype=torch.float64)
+    kz, ky, kx = torch.meshgrid(f, f, f, indexing="ij")
+    k = 2.0 * np.pi * torch.sqrt(kx * kx + ky * ky + kz * kz)
+    amp = torch.where(k > 0, k.clamp_min(1e-30) ** (0.5 * slope), torch.zeros_like(k))
+    del kx, ky, kz, k
+    g = torch.fft.ifftn(torch.fft.fftn(white) * amp).real
+    g -= g.mean()
+    s = g.std()
+    return g / s if float(s) > 0 else g
+
+
+def lognormal(n, sigma=0.5, seed=0, amp=0.5, background=1.0, device=None):
     """Density = background + amp * lognormal(sigma) field (mean of the
-    exponential is 1)."""
+    exponential is 1).  With ``device`` (a torch device) the FFTs run there and
+    a float32 torch tensor on that device is returned."""
     rng = np.random.Generator(np.random.PCG64(seed))
+    if device is not None:
+        import torch
+        g = gaussian_field_torch(n, rng, device)
+        return (background + amp * torch.exp(sigma * g - 0.5 * sigma * sigma)).float().contiguous()
     g = gaussian_field(n, rng)
     rho = background + amp * np.exp(sigma * g - 0.5 * sigma * sigma)
     return np.ascontiguousarray(rho, dtype=np.float32)
@@ -79,6 +100,35 @@ def plummer(n, n_clumps=512, seed=0, a_min=0.5, a_max=8.0, decades=2.0,
     return np.ascontiguousarray(rho, dtype=np.float32)
 
 
+def plummer_torch(base, n_clumps, seed, a_min=0.5, a_max=8.0, decades=2.0, background=1.0):
+    """``plummer`` evaluated on a torch device: ``base`` is the (n,n,n) float
+    tensor the clumps are added to (in place, returned).  Same parameter draws
+    and profile as ``plummer``."""
+    import torch
+    dev = base.device
+    n = base.shape[0]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    centres = rng.random((n_clumps, 3)) * n
+    a = np.exp(rng.uniform(np.log(a_min), np.log(a_max), n_clumps))
+    lm = rng.uniform(0.0, decades * np.log(10.0), n_clumps)
+    mass = np.exp(lm)
+    mass *= background * n ** 3 / mass.sum()
+    acc = base.double().reshape(-1)
+    for c, ac, mc in zip(centres, a, mass):
+        w = int(min(n // 2 - 1, np.ceil(8.0 * ac)))
+        lo = np.floor(c).astype(np.int64) - w
+        idx = [torch.arange(int(lo[i]), int(lo[i]) + 2 * w + 2, device=dev) for i in range(3)]
+        d = [((ix.double() + 0.5 - float(c[i])) + 0.5 * n) % n - 0.5 * n for i, ix in enumerate(idx)]
+        r2 = d[2][:, None, None] ** 2 + d[1][None, :, None] ** 2 + d[0][None, None, :] ** 2
+        prof = (1.0 + r2 / (ac * ac)) ** -2.5
+        prof = torch.where(r2 > (8.0 * ac) ** 2, torch.zeros_like(prof), prof)
+        prof *= mc / prof.sum()
+        iz, iy, ix = idx[2] % n, idx[1] % n, idx[0] % n
+        flat = (iz[:, None, None] * n + iy[None, :, None]) * n + ix[None, None, :]
+        acc.index_add_(0, flat.reshape(-1), prof.reshape(-1))
+    return acc.reshape(n, n, n).float().contiguous()
+
+
 def point(n, cell=(0, 0, 0)):
     """Unit mass in one cell ((z, y, x) index); rho = n^3 there."""
     rho = np.zeros((n, n, n), dtype=np.float32)
@@ -109,3 +159,15 @@ def config_density(config, n=None, field=0):
     if config == 5:            # the 256^3 headline workload: lognormal sigma 0.5
         return lognormal(n or 256, sigma=0.5, seed=seed)
     raise ValueError(f"unknown config {config}")
+
+
+def config_density_torch(config, device, n=None, field=0):
+    """config_density on a torch device (float32 tensor); configs 4 and 5."""
+    seed = 1000 * int(config) + int(field)
+    if config == 4:
+        nn = n or 512
+        base = lognormal(nn, sigma=1.5, seed=seed, amp=1.0, background=1.0, device=device)
+        return plummer_torch(base, 4096, seed + 1)
+    if config == 5:
+        return lognormal(n or 256, sigma=0.5, seed=seed, device=device)
+    raise ValueError(f"no device recipe for config {config}")
