@@ -27,9 +27,45 @@ def test_two_level_tree_with_gridlet_equal_subgrid_is_exact(n):
     assert _rel(g, g_ref) < 1e-12
 
 
-def test_p2m_identity_when_gridlet_is_subgrid_and_monopole_when_p_is_1():
-    np.testing.assert_allclose(fmm.p2m_matrix(4, 4), np.eye(64), atol=1e-12)
-    np.testing.assert_allclose(fmm.p2m_matrix(4, 1), np.ones((1, 64)), atol=1e-13)
+@pytest.mark.parametrize("p", [4, 6, 8])
+def test_p2m_identity_when_gridlet_is_subgrid_and_monopole_when_p_is_1(p):
+    np.testing.assert_allclose(fmm.p2m_matrix(p, p), np.eye(p ** 3), atol=1e-12)
+    np.testing.assert_allclose(fmm.p2m_matrix(p, 1), np.ones((1, p ** 3)), atol=1e-13)
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_per_axis_solve_equals_the_three_dimensional_vandermonde_system(p):
+    # Sec. 2 defines the gridlet masses by V M = Q over all multi-indices
+    # n_i < p; where that 3-D system is well conditioned its direct solution
+    # must equal the per-axis (tensor-product) solution the oracle uses.
+    cells = fmm.tensor_points((np.arange(8) + 0.5) / 8 - 0.5)
+    direct = np.linalg.solve(fmm.vandermonde(p), fmm.moment_matrix(cells, p))
+    np.testing.assert_allclose(fmm.p2m_matrix(8, p), direct, atol=1e-9)
+    pts = fmm.tensor_points(fmm.gridlet_offsets(p)) / 2.0 + (np.array([1, 0, 1]) - 0.5) / 2.0
+    direct = np.linalg.solve(fmm.vandermonde(p), fmm.moment_matrix(pts, p))
+    np.testing.assert_allclose(fmm.m2m_matrix(p, (1, 0, 1)), direct, atol=1e-9)
+
+
+@pytest.mark.parametrize("p", [5, 8])
+def test_gridlet_masses_are_the_lagrange_basis_at_high_order(p):
+    # The 1-D Vandermonde solution is the Lagrange basis of the gridlet points
+    # (closed form, no linear solve): T[s, j] = prod_{k != s} (x_j - g_k) / (g_s - g_k).
+    g = fmm.gridlet_offsets(p)
+    for S in (p, 2 * p, 24):
+        x = (np.arange(S) + 0.5) / S - 0.5
+        T1 = np.ones((p, S))
+        for s_ in range(p):
+            for k in range(p):
+                if k != s_:
+                    T1[s_] *= (x - g[k]) / (g[s_] - g[k])
+        want = np.kron(T1, np.kron(T1, T1))
+        np.testing.assert_allclose(fmm.p2m_matrix(S, p), want, atol=1e-11 * np.abs(want).max())
+    # M2M: moments n_i < p of the child gridlet are preserved (relative to scale)
+    for child in [(0, 0, 0), (1, 0, 1), (1, 1, 1)]:
+        pts = fmm.tensor_points(g) / 2.0 + (np.array(child) - 0.5) / 2.0
+        W_child = fmm.moment_matrix(pts, p)
+        got = fmm.vandermonde(p) @ fmm.m2m_matrix(p, child)
+        np.testing.assert_allclose(got, W_child, atol=1e-12 * np.abs(fmm.m2m_matrix(p, child)).max())
 
 
 def test_p2m_two_points_per_dimension_closed_form():
@@ -49,7 +85,7 @@ def test_p2m_two_points_per_dimension_closed_form():
         np.testing.assert_allclose(col, exp, atol=1e-13)
 
 
-@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("p", [2, 3, 4, 6, 8])
 def test_m2m_after_p2m_equals_p2m_to_the_parent(p):
     rho = inputs.lognormal(16, sigma=1.0, seed=7)
     m = pm.masses(rho)
