@@ -123,6 +123,16 @@ int fmm_plan_inject_fault(fmm_plan* plan, int kind);
  * FMM_ERR_ARG outside 1..189. */
 int fmm_plan_set_m2l_group(fmm_plan* plan, int offsets_per_partial);
 
+/* Mixed-precision forms: the first tree level whose M2L (eq. fmm2) runs on
+ * the tensor cores; coarser levels run the FP32 CUDA-core kernel.  Default
+ * and minimum 4 (levels 2 and 3 always use the split-table FP32 kernel); a
+ * value above the leaf level L keeps every level on the CUDA cores.  At high
+ * order (p >= 7) the gridlet masses of non-leaf nodes are large alternating
+ * sums (Lagrange extrapolation to the node edges), which BF16 splits round
+ * badly; putting only the leaf level (tc_min_level = L) on the tensor cores
+ * keeps most of the speed.  FMM_ERR_ARG outside 4..9. */
+int fmm_plan_set_tc_min_level(fmm_plan* plan, int level);
+
 /* Synchronise the device and read the plan's device error word: FMM_OK, or
  * FMM_ERR_TIMEOUT if a bounded device-side wait of an earlier solve gave up
  * (the word is then cleared).  Solves never block forever. */

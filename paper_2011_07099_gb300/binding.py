@@ -51,6 +51,7 @@ SIGNATURES = {
     "fmm_plan_set_timing": (_I, [_VP, _I]),
     "fmm_plan_check": (_I, [_VP]),
     "fmm_plan_set_m2l_group": (_I, [_VP, _I]),
+    "fmm_plan_set_tc_min_level": (_I, [_VP, _I]),
     "fmm_plan_set_timeout_ms": (_I, [_VP, _I]),
     "fmm_plan_inject_fault": (_I, [_VP, _I]),
     "fmm_mean_density_noalloc": (_I, [_FP, _SZ, _FP, _VP]),
@@ -150,6 +151,10 @@ def fmm_plan_copy_stage(plan, stage, level, dst, stream=None):
 
 def fmm_plan_set_m2l_group(plan, offsets_per_partial):
     _check(lib().fmm_plan_set_m2l_group(plan, int(offsets_per_partial)), "fmm_plan_set_m2l_group")
+
+
+def fmm_plan_set_tc_min_level(plan, level):
+    _check(lib().fmm_plan_set_tc_min_level(plan, int(level)), "fmm_plan_set_tc_min_level")
 
 
 def fmm_plan_set_timeout_ms(plan, ms):

@@ -314,6 +314,12 @@ int fmm_plan_set_m2l_group(fmm_plan* plan, int offsets_per_partial) {
   return set_err(FMM_OK);
 }
 
+int fmm_plan_set_tc_min_level(fmm_plan* plan, int level) {
+  if (!plan || level < fmm::kTcMinLevel || level > fmm::kMaxLevel + 1) return set_err(FMM_ERR_ARG);
+  reinterpret_cast<Plan*>(plan)->tc_min_level = level;
+  return set_err(FMM_OK);
+}
+
 int fmm_plan_set_correction_inference(fmm_plan* plan, int mode) {
   if (!plan || (mode != FMM_INFER_BF16 && mode != FMM_INFER_FP32)) return set_err(FMM_ERR_ARG);
   reinterpret_cast<Plan*>(plan)->corr_fp32 = mode == FMM_INFER_FP32 ? 1 : 0;
@@ -445,7 +451,7 @@ int fmm_solve(fmm_plan* plan, const float* density, float* potential, float* acc
   const bool tc = P.prec != FMM_PREC_FP32 && P.tc_ready;
   for (int l = 2; l <= P.L; ++l) {
     FMM_CUDA_TRY(mark(FMM_TIME_M2L_LEVEL0 + l, 0));
-    if (tc && l >= fmm::kTcMinLevel) {
+    if (tc && l >= P.tc_min_level) {
       FMM_CUDA_TRY(fmm::launch_split_bf16(P, l, s));
       FMM_CUDA_TRY(fmm::launch_m2l_tc(P, l, P.prec, s));
     } else {

@@ -67,7 +67,7 @@ struct Plan {
   float* M[kMaxLevel + 1] = {};     // gridlet masses, 8^l x p^3, levels 2..L
   float* F[kMaxLevel + 1] = {};     // local fields, 8^l x 4 x p^3, levels 2..L
   float4* tab[kMaxLevel + 1] = {};  // (G, -dG/dx, -dG/dy, -dG/dz) at n dx_l, n in [-(4p-1), 4p-1]^3
-  float* tab_lo[kMaxLevel + 1] = {};  // G - fl32(G) of the same entries (levels 2..kExtLevels+1)
+  float4* tab_lo[kMaxLevel + 1] = {};  // v - fl32(v) of the same entries, 4 fields (levels 2..kExtTopLevel)
   float4* near_tab = nullptr;       // the same at cell spacing for |d_i| in [0, 2S-1], folded
   float2* w_p2m = nullptr;          // Lagrange weights [p][S] as (hi, lo): gridlet s at cell c
   float2* w_m2m = nullptr;          // Lagrange weights [p][2p] as (hi, lo): parent s at child point u
@@ -80,6 +80,7 @@ struct Plan {
   void* Mbf_lo[kMaxLevel + 1] = {};        // unused (kept null)
   void* Apre[kMaxLevel + 1] = {};          // precomputed split translation tiles per offset slot
   int tc_group = 2;                        // offsets accumulated per TMEM partial before promotion
+  int tc_min_level = kTcMinLevel;          // first level on the tensor cores in the mixed forms
   // learned table correction (MLP weights) and its training buffers
   float* corr_w = nullptr;                 // mlp::kParams weights (device) or unset
   int has_corr = 0;

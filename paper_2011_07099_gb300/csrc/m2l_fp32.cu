@@ -23,7 +23,9 @@
 // into planes, and each plane is added to the total with Kahan compensation.
 // At the top two levels the potential also takes the low half of the split
 // table, G = G_hi + G_lo: rounding G to FP32 errs coherently across targets
-// and is the largest remaining error of the long-range potential.
+// and is the largest remaining error of the long-range potential.  At high
+// order (p >= 7) the rounding of the gradient tables matters as well (1.5e-5
+// on g at p = 8), so all four fields take their low halves there (EXT = 2).
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -36,10 +38,12 @@ struct M2LShape {
   static constexpr int NT = P3 > 256 ? 4 : 8;            // targets per CTA (register budget)
 };
 
-template <int P, bool EXT>
+// EXT: 0 = FP32 table; 1 = the potential also takes G_lo; 2 = all four fields
+// take their low halves.
+template <int P, int EXT>
 __global__ void __launch_bounds__(M2LShape<P>::THREADS)
 k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __restrict__ tab,
-           const float* __restrict__ tab_lo, const int8_t* __restrict__ offs, int n_off, int level) {
+           const float4* __restrict__ tab_lo, const int8_t* __restrict__ offs, int n_off, int level) {
   constexpr int P3 = P * P * P;
   constexpr int NT = M2LShape<P>::NT;
   constexpr int D = 2 * P - 1;          // table window per dimension
@@ -48,7 +52,8 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
   extern __shared__ float4 sm4[];
   float4* win = sm4;                                     // D3 float4
   float4* msrc = win + D3;                               // P3 x (NT/4) float4: [s][k]
-  float* win_lo = reinterpret_cast<float*>(msrc + P3 * (NT / 4));   // D3 (EXT only)
+  float* win_lo = reinterpret_cast<float*>(msrc + P3 * (NT / 4));   // D3 floats (EXT == 1)
+  float4* win_lo4 = msrc + P3 * (NT / 4);                            // D3 float4 (EXT == 2)
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int ctype = blockIdx.y;
   const int n = 1 << level;
@@ -80,7 +85,8 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
       const int dx = i % D - (P - 1), dy = (i / D) % D - (P - 1), dz = i / (D * D) - (P - 1);
       const int nx = ox * P + dx + HW, ny = oy * P + dy + HW, nz = oz * P + dz + HW;
       win[i] = __ldg(tab + ((size_t)nz * E + ny) * E + nx);
-      if (EXT) win_lo[i] = __ldg(tab_lo + ((size_t)nz * E + ny) * E + nx);
+      if (EXT == 1) win_lo[i] = __ldg(&tab_lo[((size_t)nz * E + ny) * E + nx].x);
+      if (EXT == 2) win_lo4[i] = __ldg(tab_lo + ((size_t)nz * E + ny) * E + nx);
     }
     float* ms = reinterpret_cast<float*>(msrc);
     for (int i = tid; i < NT * P3; i += nthr) {
@@ -95,9 +101,12 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
     }
     __syncthreads();
     if (r < P3) {
-      float plo[NT];
+      constexpr int NLO = EXT == 2 ? 4 : 1;
+      float plo[NLO][NT];
 #pragma unroll
-      for (int k = 0; k < NT; ++k) plo[k] = 0.f;
+      for (int f = 0; f < NLO; ++f)
+#pragma unroll
+        for (int k = 0; k < NT; ++k) plo[f][k] = 0.f;
 #pragma unroll 1
       for (int sz = 0; sz < P; ++sz) {
         float plane[4][NT];
@@ -117,7 +126,7 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
             const int s = (sz * P + sy) * P + sx;
             const int w = rbase - ((sz * D + sy) * D + sx);
             const float4 t = win[w];
-            const float tl = EXT ? win_lo[w] : 0.f;
+            const float4 tl = EXT == 2 ? win_lo4[w] : make_float4(EXT == 1 ? win_lo[w] : 0.f, 0.f, 0.f, 0.f);
             const float4* mv = msrc + s * (NT / 4);
 #pragma unroll
             for (int q = 0; q < NT / 4; ++q) {
@@ -129,7 +138,12 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
                 row[1][4 * q + j] = fmaf(t.y, mm[j], row[1][4 * q + j]);
                 row[2][4 * q + j] = fmaf(t.z, mm[j], row[2][4 * q + j]);
                 row[3][4 * q + j] = fmaf(t.w, mm[j], row[3][4 * q + j]);
-                if (EXT) plo[4 * q + j] = fmaf(tl, mm[j], plo[4 * q + j]);
+                if (EXT >= 1) plo[0][4 * q + j] = fmaf(tl.x, mm[j], plo[0][4 * q + j]);
+                if (EXT == 2) {
+                  plo[NLO - 3][4 * q + j] = fmaf(tl.y, mm[j], plo[NLO - 3][4 * q + j]);
+                  plo[NLO - 2][4 * q + j] = fmaf(tl.z, mm[j], plo[NLO - 2][4 * q + j]);
+                  plo[NLO - 1][4 * q + j] = fmaf(tl.w, mm[j], plo[NLO - 1][4 * q + j]);
+                }
               }
             }
           }
@@ -151,7 +165,9 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
       }
       if (EXT) {
 #pragma unroll
-        for (int k = 0; k < NT; ++k) comp[0][k] -= plo[k];
+        for (int f = 0; f < NLO; ++f)
+#pragma unroll
+          for (int k = 0; k < NT; ++k) comp[f][k] -= plo[f][k];
       }
     }
   }
@@ -171,25 +187,28 @@ cudaError_t launch_p(Plan& Pl, int level, cudaStream_t s) {
   constexpr int P3 = P * P * P;
   constexpr int D = 2 * P - 1;
   constexpr int NT = M2LShape<P>::NT;
+  constexpr int EXT_TOP = P >= 7 ? 2 : 1;
   const int threads = M2LShape<P>::THREADS;
   const bool ext = level <= kExtTopLevel;
-  const size_t smem = sizeof(float4) * (D * D * D + P3 * (NT / 4)) + (ext ? sizeof(float) * D * D * D : 0);
+  const size_t lo_bytes = ext ? (EXT_TOP == 2 ? sizeof(float4) : sizeof(float)) * D * D * D : 0;
+  const size_t smem = sizeof(float4) * (D * D * D + P3 * (NT / 4)) + lo_bytes;
   const uint32_t n_par = 1u << (3 * (level - 1));
   dim3 grid((n_par + NT - 1) / NT, 8);
   if (ext)
-    k_m2l_fp32<P, true><<<grid, threads, smem, s>>>(Pl.M[level], Pl.F[level], Pl.tab[level], Pl.tab_lo[level],
-                                                    Pl.offsets[level], Pl.n_off[level], level);
+    k_m2l_fp32<P, EXT_TOP><<<grid, threads, smem, s>>>(Pl.M[level], Pl.F[level], Pl.tab[level], Pl.tab_lo[level],
+                                                       Pl.offsets[level], Pl.n_off[level], level);
   else
-    k_m2l_fp32<P, false><<<grid, threads, smem, s>>>(Pl.M[level], Pl.F[level], Pl.tab[level], nullptr,
-                                                     Pl.offsets[level], Pl.n_off[level], level);
+    k_m2l_fp32<P, 0><<<grid, threads, smem, s>>>(Pl.M[level], Pl.F[level], Pl.tab[level], nullptr,
+                                                 Pl.offsets[level], Pl.n_off[level], level);
   return cudaGetLastError();
 }
 
 template <int P>
 cudaError_t setup_p() {
-  cudaError_t e = cudaFuncSetAttribute(k_m2l_fp32<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  constexpr int EXT_TOP = P >= 7 ? 2 : 1;
+  cudaError_t e = cudaFuncSetAttribute(k_m2l_fp32<P, EXT_TOP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_m2l_fp32<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  return cudaFuncSetAttribute(k_m2l_fp32<P, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 }  // namespace

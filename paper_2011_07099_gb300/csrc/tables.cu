@@ -55,7 +55,7 @@ __device__ inline void add_correction(double v[4], int ix, int iy, int iz, int l
 // (Sec. 3: gridlet spacing of a level-l node; the (4 N_g)^D samples of Sec. 4
 // folded over the sign of each component).  Entry n = 0 is never used by M2L
 // (the interaction zone excludes near nodes) and is stored as 0.
-__global__ void k_tab_m2l(float4* __restrict__ out, float* __restrict__ lo, int p, int level, const float* mlp,
+__global__ void k_tab_m2l(float4* __restrict__ out, float4* __restrict__ lo, int p, int level, const float* mlp,
                           int fp32) {
   const int hw = 4 * p - 1, E = 8 * p - 1;
   const long total = (long)E * E * E;
@@ -66,7 +66,9 @@ __global__ void k_tab_m2l(float4* __restrict__ out, float* __restrict__ lo, int 
     if (ix | iy | iz) gs1(ix * dx, iy * dx, iz * dx, v);
     add_correction(v, ix, iy, iz, level, p, mlp, fp32);
     out[i] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
-    if (lo) lo[i] = (float)(v[0] - (double)(float)v[0]);
+    if (lo)
+      lo[i] = make_float4((float)(v[0] - (double)(float)v[0]), (float)(v[1] - (double)(float)v[1]),
+                          (float)(v[2] - (double)(float)v[2]), (float)(v[3] - (double)(float)v[3]));
   }
 }
 
