@@ -90,12 +90,14 @@ std::vector<int8_t> interaction_offsets(int level, int c) {
 void free_plan(Plan* P) {
   if (!P) return;
   cudaFree(P->d_partials);
+  cudaFree(P->m2l_part);
   cudaFree(P->d_mean);
   for (int l = 0; l <= fmm::kMaxLevel; ++l) {
     cudaFree(P->M[l]);
     cudaFree(P->F[l]);
     cudaFree(P->tab[l]);
     cudaFree(P->tab_lo[l]);
+    cudaFree(P->F64[l]);
     cudaFree(P->offsets[l]);
   }
   cudaFree(P->near_tab);
@@ -234,6 +236,22 @@ fmm_plan* fmm_plan_create(int N, int L, int order) {
     free_plan(P);
     set_err(FMM_ERR_INTERNAL);
     return nullptr;
+  }
+  {
+    // scratch for the offset-range partials of the coarse FP32 M2L levels
+    size_t part = 0;
+    for (int l = 2; l <= L; ++l) {
+      if (l > fmm::kExtTopLevel) continue;
+      const int ns = fmm::m2l_fp32_splits(*P, l);
+      const size_t need = 2 * (size_t)ns * ((size_t)1 << (3 * l)) * 4 * p3;
+      if (need > part) part = need;
+      if (!dev_alloc(&P->F64[l], ((size_t)1 << (3 * l)) * 4 * p3)) part = 0;
+    }
+    if (!part || !dev_alloc(&P->m2l_part, part)) {
+      free_plan(P);
+      set_err(FMM_ERR_ALLOC);
+      return nullptr;
+    }
   }
   if (fmm::setup_upward(*P) != cudaSuccess || fmm::setup_m2l_fp32(*P) != cudaSuccess ||
       fmm::setup_m2l_tc(*P) != cudaSuccess || fmm::setup_learn() != cudaSuccess ||

@@ -36,9 +36,49 @@ __global__ void k_l2l(const float* __restrict__ Fp, int p, const float2* __restr
   }
 }
 
+// FP64 variant for parents at the coarse levels (<= kExtTopLevel), one field
+// at a time (shared memory).  The child field is F64 (a coarse child, whose
+// FP32 copy is refreshed too) or the FP32 field of the first fine level, to
+// which the FP64 contribution is added before a single rounding.
+__global__ void k_l2l64(const double* __restrict__ Fp, int p, const double* __restrict__ w,
+                        double* __restrict__ Fc64, float* __restrict__ Fc) {
+  extern __shared__ double smd[];
+  const int K = 2 * p, p3 = p * p * p;
+  double* W = smd;                  // p*K  ([p][2p], used transposed)
+  double* in = W + p * K;           // p^3
+  double* t1 = in + p3;             // p*p*K
+  double* t2 = t1 + p * p * K;      // p*K*K
+  double* out = t2 + p * K * K;     // K^3
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int i = tid; i < p * K; i += nthr) W[i] = w[i];
+  for (int f = 0; f < 4; ++f) {
+    const double* src = Fp + ((size_t)blockIdx.x * 4 + f) * p3;
+    for (int i = tid; i < p3; i += nthr) in[i] = src[i];
+    __syncthreads();
+    contract3_d(in, t1, t2, out, p, K, W, K, tid, nthr, true);
+    for (int i = tid; i < 8 * p3; i += nthr) {
+      const int c = i / p3, q = i % p3;
+      const int qx = q % p, qy = (q / p) % p, qz = q / (p * p);
+      const int ux = (c & 1) * p + qx, uy = ((c >> 1) & 1) * p + qy, uz = (c >> 2) * p + qz;
+      const size_t d = (((size_t)blockIdx.x * 8 + c) * 4 + f) * p3 + q;
+      const double v = out[(uz * K + uy) * K + ux];
+      if (Fc64) {
+        const double t = Fc64[d] + v;
+        Fc64[d] = t;
+        Fc[d] = (float)t;
+      } else {
+        Fc[d] = (float)((double)Fc[d] + v);
+      }
+    }
+    __syncthreads();   // `in` and `out` are reused by the next field
+  }
+}
+
 }  // namespace
 
 cudaError_t setup_downward(const Plan& P) {
+  cudaError_t e = cudaFuncSetAttribute(k_l2l64, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_l2l, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
@@ -46,6 +86,12 @@ cudaError_t launch_l2l(Plan& P, int level, cudaStream_t s) {
   const int p = P.p, K = 2 * p, p3 = p * p * p;
   const size_t smem = sizeof(float2) * p * K + sizeof(float) * (4 * p3 + 4 * p * p * K + 4 * p * K * K + 4 * K * K * K);
   const unsigned parents = 1u << (3 * level);
+  if (level <= kExtTopLevel) {
+    const size_t smem64 = sizeof(double) * (p * K + p3 + p * p * K + p * K * K + K * K * K);
+    k_l2l64<<<parents, 256, smem64, s>>>(P.F64[level], p, P.wd_m2m, level + 1 <= kExtTopLevel ? P.F64[level + 1] : nullptr,
+                                         P.F[level + 1]);
+    return cudaGetLastError();
+  }
   k_l2l<<<parents, 256, smem, s>>>(P.F[level], p, P.w_m2m, P.F[level + 1]);
   return cudaGetLastError();
 }

@@ -66,6 +66,12 @@ struct Plan {
   int n_partials = 0;
   float* M[kMaxLevel + 1] = {};     // gridlet masses, 8^l x p^3, levels 2..L
   float* F[kMaxLevel + 1] = {};     // local fields, 8^l x 4 x p^3, levels 2..L
+  float* m2l_part = nullptr;        // coarse FP32 M2L levels: ranges x (sum, low part) x 8^l x 4 p^3
+  // Local fields of the levels <= kExtTopLevel in FP64: the L2L interpolation
+  // to the children extrapolates to points outside the parent's gridlet
+  // (weights up to ~160 in absolute sum at p = 6), so FP32 storage of the
+  // coarse local fields would cost ~1e-6 of the potential.
+  double* F64[kMaxLevel + 1] = {};
   float4* tab[kMaxLevel + 1] = {};  // (G, -dG/dx, -dG/dy, -dG/dz) at n dx_l, n in [-(4p-1), 4p-1]^3
   float4* tab_lo[kMaxLevel + 1] = {};  // v - fl32(v) of the same entries, 4 fields (levels 2..kExtTopLevel)
   float4* near_tab = nullptr;       // the same at cell spacing for |d_i| in [0, 2S-1], folded
@@ -112,6 +118,8 @@ struct Plan {
 // plan creation, never inside a solve, so a solve is safe to capture.
 cudaError_t setup_upward(const Plan& P);
 cudaError_t setup_m2l_fp32(const Plan& P);
+// Number of offset ranges the FP32 M2L of a level is split into (1 = none).
+int m2l_fp32_splits(const Plan& P, int level);
 cudaError_t setup_downward(const Plan& P);
 cudaError_t setup_p2p(const Plan& P);
 
@@ -121,7 +129,7 @@ cudaError_t launch_tables(Plan& P, cudaStream_t s);
 cudaError_t launch_mean(Plan& P, const float* rho, cudaStream_t s);
 cudaError_t launch_p2m(Plan& P, const float* rho, cudaStream_t s);
 cudaError_t launch_m2m(Plan& P, int level, cudaStream_t s);       // level+1 -> level
-cudaError_t launch_m2l_fp32(Plan& P, int level, cudaStream_t s);  // writes F[level]
+cudaError_t launch_m2l_fp32(Plan& P, int level, cudaStream_t s);  // writes F[level] (and F64[level] when coarse)
 cudaError_t launch_l2l(Plan& P, int level, cudaStream_t s);       // F[level] -> F[level+1] (adds)
 cudaError_t launch_p2p(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s);
 cudaError_t setup_m2l_tc(const Plan& P);
@@ -171,7 +179,8 @@ __device__ inline void contract_mid(const float* __restrict__ in, float* __restr
 // rounds the same way in FP32, so those errors add up coherently across the
 // mesh instead of averaging out.
 __device__ inline void contract_mid_d(const double* __restrict__ in, double* __restrict__ out, int A, int Kin,
-                                      int Kout, int B, const double* __restrict__ W, int ldw, int tid, int nthr) {
+                                      int Kout, int B, const double* __restrict__ W, int ldw, int tid, int nthr,
+                                      bool wt = false) {
   const int total = A * Kout * B;
   for (int i = tid; i < total; i += nthr) {
     const int b = i % B;
@@ -179,18 +188,18 @@ __device__ inline void contract_mid_d(const double* __restrict__ in, double* __r
     const int a = i / (B * Kout);
     const double* src = in + (size_t)a * Kin * B + b;
     double acc = 0.0;
-    for (int k = 0; k < Kin; ++k) acc = fma(W[s * ldw + k], src[k * B], acc);
+    for (int k = 0; k < Kin; ++k) acc = fma(wt ? W[k * ldw + s] : W[s * ldw + k], src[k * B], acc);
     out[i] = acc;
   }
 }
 
 __device__ inline void contract3_d(const double* in, double* t1, double* t2, double* out, int Kin, int Kout,
-                                   const double* W, int ldw, int tid, int nthr) {
-  contract_mid_d(in, t1, Kin * Kin, Kin, Kout, 1, W, ldw, tid, nthr);
+                                   const double* W, int ldw, int tid, int nthr, bool wt = false) {
+  contract_mid_d(in, t1, Kin * Kin, Kin, Kout, 1, W, ldw, tid, nthr, wt);
   __syncthreads();
-  contract_mid_d(t1, t2, Kin, Kin, Kout, Kout, W, ldw, tid, nthr);
+  contract_mid_d(t1, t2, Kin, Kin, Kout, Kout, W, ldw, tid, nthr, wt);
   __syncthreads();
-  contract_mid_d(t2, out, 1, Kin, Kout, Kout * Kout, W, ldw, tid, nthr);
+  contract_mid_d(t2, out, 1, Kin, Kout, Kout * Kout, W, ldw, tid, nthr, wt);
   __syncthreads();
 }
 

@@ -9,8 +9,12 @@
 // offset's translation matrix is a window of the level table.
 //
 // Work split: a CTA owns NT targets of one child type (the 8 types have
-// different interaction lists, Sec. 2 Fig. fmm); thread r owns one target
-// gridlet point and keeps NT x 4 accumulators.  Per offset the CTA stages the
+// different interaction lists, Sec. 2 Fig. fmm) and one contiguous range of
+// the interaction offsets; thread r owns one target gridlet point and keeps
+// NT x 4 accumulators.  The coarse levels have few targets (64 at level 2,
+// 512 at level 3), so there the offsets are split over enough CTAs to fill
+// the GPU, each range writes its own partial field, and a second kernel adds
+// the partials in range order.  Per offset the CTA stages the
 // (2p-1)^3 table window and the NT source gridlets in shared memory, so every
 // table value read feeds 4 x NT FMAs and every mass read (a broadcast) feeds 4.
 //
@@ -43,7 +47,8 @@ struct M2LShape {
 template <int P, int EXT>
 __global__ void __launch_bounds__(M2LShape<P>::THREADS)
 k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __restrict__ tab,
-           const float4* __restrict__ tab_lo, const int8_t* __restrict__ offs, int n_off, int level) {
+           const float4* __restrict__ tab_lo, const int8_t* __restrict__ offs, int n_off, int level,
+           int per_split, size_t split_stride, int pairs) {
   constexpr int P3 = P * P * P;
   constexpr int NT = M2LShape<P>::NT;
   constexpr int D = 2 * P - 1;          // table window per dimension
@@ -60,6 +65,11 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
   const uint32_t n_par = 1u << (3 * (level - 1));
   const uint32_t par0 = blockIdx.x * NT;
   const int8_t* my_offs = offs + (size_t)ctype * n_off * 3;
+  const int io0 = blockIdx.z * per_split;
+  const int io1 = io0 + per_split < n_off ? io0 + per_split : n_off;
+  // with `pairs`, each range writes (sum, -compensation): [range][hi | lo][field]
+  const bool split = pairs != 0;
+  F += 2 * (size_t)blockIdx.z * split_stride;
 
   __shared__ int tx[NT], ty[NT], tz[NT];
   if (tid < NT) {
@@ -78,9 +88,10 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
   const int rx = r % P, ry = (r / P) % P, rz = r / (P * P);
   const int rbase = ((rz + P - 1) * D + (ry + P - 1)) * D + (rx + P - 1);
 
-  for (int io = 0; io < n_off; ++io) {
+  __syncthreads();     // tx.. are set (also when the range is empty)
+  for (int io = io0; io < io1; ++io) {
     const int ox = my_offs[3 * io + 0], oy = my_offs[3 * io + 1], oz = my_offs[3 * io + 2];
-    __syncthreads();   // previous offset's compute is done with the buffers (and tx.. are set)
+    __syncthreads();   // previous offset's compute is done with the buffers
     for (int i = tid; i < D3; i += nthr) {
       const int dx = i % D - (P - 1), dy = (i / D) % D - (P - 1), dz = i / (D * D) - (P - 1);
       const int nx = ox * P + dx + HW, ny = oy * P + dy + HW, nz = oz * P + dz + HW;
@@ -177,8 +188,151 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
       if (par0 + k >= n_par) break;
       float* dst = F + (size_t)(8u * (par0 + k) + ctype) * 4 * P3;
 #pragma unroll
-      for (int f = 0; f < 4; ++f) dst[f * P3 + r] = acc[f][k];
+      for (int f = 0; f < 4; ++f) {
+        if (split) {
+          dst[f * P3 + r] = acc[f][k];
+          dst[split_stride + f * P3 + r] = -comp[f][k];
+        } else {
+          dst[f * P3 + r] = acc[f][k] - comp[f][k];
+        }
+      }
     }
+  }
+}
+
+// Level 2 (the first far-field level, 37 periodic interaction nodes, Sec. 2)
+// carries the long-range potential: its terms are ~100 times larger than the
+// potential they sum to, so FP32 products alone cost ~1e-6.  This kernel sums
+// eq. fmm2 there in double-float arithmetic: every product with the split
+// table value G_hi + G_lo is accumulated as an unevaluated sum (s, c) with
+// error-free transformations (TwoProd by FMA, TwoSum; Ogita, Rump and Oishi,
+// "Accurate sum and dot product", 2005), about 48 significant bits in FP32
+// instructions; the FP64 pipe of this part would be ~6x slower.
+template <int P>
+__global__ void __launch_bounds__(M2LShape<P>::THREADS)
+k_m2l_df(const float* __restrict__ M, float* __restrict__ F, const float4* __restrict__ tab,
+         const float4* __restrict__ tab_lo, const int8_t* __restrict__ offs, int n_off, int level, int per_split,
+         size_t split_stride, int pairs) {
+  constexpr int P3 = P * P * P;
+  constexpr int NT = M2LShape<P>::NT;
+  constexpr int D = 2 * P - 1;
+  constexpr int D3 = D * D * D;
+  constexpr int HW = 4 * P - 1, E = 8 * P - 1;
+  extern __shared__ float4 sm4[];
+  float4* win = sm4;                       // D3
+  float4* wlo = win + D3;                  // D3
+  float4* msrc = wlo + D3;                 // P3 x (NT/4): [s][k]
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int ctype = blockIdx.y;
+  const int n = 1 << level;
+  const uint32_t n_par = 1u << (3 * (level - 1));
+  const uint32_t par0 = blockIdx.x * NT;
+  const int8_t* my_offs = offs + (size_t)ctype * n_off * 3;
+  const int io0 = blockIdx.z * per_split;
+  const int io1 = io0 + per_split < n_off ? io0 + per_split : n_off;
+  const bool split = pairs != 0;
+  F += 2 * (size_t)blockIdx.z * split_stride;
+
+  __shared__ int tx[NT], ty[NT], tz[NT];
+  if (tid < NT) {
+    uint32_t x = 0, y = 0, z = 0;
+    if (par0 + tid < n_par) unmorton(8u * (par0 + tid) + ctype, x, y, z);
+    tx[tid] = x; ty[tid] = y; tz[tid] = z;
+  }
+  float hs[4][NT], lc[4][NT];
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int k = 0; k < NT; ++k) hs[f][k] = lc[f][k] = 0.f;
+  const int r = tid;
+  const int rx = r % P, ry = (r / P) % P, rz = r / (P * P);
+  const int rbase = ((rz + P - 1) * D + (ry + P - 1)) * D + (rx + P - 1);
+
+  __syncthreads();
+  for (int io = io0; io < io1; ++io) {
+    const int ox = my_offs[3 * io + 0], oy = my_offs[3 * io + 1], oz = my_offs[3 * io + 2];
+    __syncthreads();
+    for (int i = tid; i < D3; i += nthr) {
+      const int dx = i % D - (P - 1), dy = (i / D) % D - (P - 1), dz = i / (D * D) - (P - 1);
+      const size_t g = ((size_t)(oz * P + dz + HW) * E + (oy * P + dy + HW)) * E + (ox * P + dx + HW);
+      win[i] = __ldg(tab + g);
+      wlo[i] = __ldg(tab_lo + g);
+    }
+    float* ms = reinterpret_cast<float*>(msrc);
+    for (int i = tid; i < NT * P3; i += nthr) {
+      const int k = i / P3, s = i % P3;
+      float v = 0.f;
+      if (par0 + k < n_par) {
+        const uint32_t sx = (uint32_t)(tx[k] - ox) & (n - 1), sy = (uint32_t)(ty[k] - oy) & (n - 1),
+                       sz = (uint32_t)(tz[k] - oz) & (n - 1);
+        v = __ldg(M + (size_t)morton(sx, sy, sz) * P3 + s);
+      }
+      ms[s * NT + k] = v;
+    }
+    __syncthreads();
+    if (r < P3) {
+#pragma unroll 1
+      for (int sz = 0; sz < P; ++sz)
+#pragma unroll 1
+        for (int sy = 0; sy < P; ++sy)
+#pragma unroll
+          for (int sx = 0; sx < P; ++sx) {
+            const int s = (sz * P + sy) * P + sx;
+            const int w = rbase - ((sz * D + sy) * D + sx);
+            const float4 th = win[w], tl = wlo[w];
+            const float gh[4] = {th.x, th.y, th.z, th.w}, gl[4] = {tl.x, tl.y, tl.z, tl.w};
+            const float4* mv = msrc + s * (NT / 4);
+#pragma unroll
+            for (int q = 0; q < NT / 4; ++q) {
+              const float4 m4 = mv[q];
+              const float mm[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int k = 4 * q + j;
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                  // _rn intrinsics: the compiler must not contract these into FMAs
+                  const float pr = __fmul_rn(gh[f], mm[j]);
+                  const float pe = fmaf(gh[f], mm[j], -pr);          // exact product error
+                  const float t = __fadd_rn(hs[f][k], pr);            // TwoSum(hs, pr)
+                  const float z = __fsub_rn(t, hs[f][k]);
+                  const float se = __fadd_rn(__fsub_rn(hs[f][k], __fsub_rn(t, z)), __fsub_rn(pr, z));
+                  hs[f][k] = t;
+                  lc[f][k] = fmaf(gl[f], mm[j], __fadd_rn(lc[f][k], __fadd_rn(pe, se)));
+                }
+              }
+            }
+          }
+    }
+  }
+  if (r < P3) {
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      if (par0 + k >= n_par) break;
+      float* dst = F + (size_t)(8u * (par0 + k) + ctype) * 4 * P3;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        if (split) {
+          dst[f * P3 + r] = hs[f][k];
+          dst[split_stride + f * P3 + r] = lc[f][k];
+        } else {
+          dst[f * P3 + r] = hs[f][k] + lc[f][k];
+        }
+      }
+    }
+  }
+}
+
+// Coarse levels: F64[i] = sum over the offset ranges z = 0, 1, ... of the
+// range sums part[z][0][i] plus their low parts part[z][1][i], in FP64 (the
+// ranges' partial sums cancel heavily); F[i] gets the FP32 rounding.
+__global__ void k_sum_ranges(const float* __restrict__ part, int nsplit, size_t n, double* __restrict__ F64,
+                             float* __restrict__ F) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int z = 0; z < nsplit; ++z) v += (double)part[2 * z * n + i] + (double)part[(2 * z + 1) * n + i];
+    F64[i] = v;
+    F[i] = (float)v;
   }
 }
 
@@ -193,25 +347,46 @@ cudaError_t launch_p(Plan& Pl, int level, cudaStream_t s) {
   const size_t lo_bytes = ext ? (EXT_TOP == 2 ? sizeof(float4) : sizeof(float)) * D * D * D : 0;
   const size_t smem = sizeof(float4) * (D * D * D + P3 * (NT / 4)) + lo_bytes;
   const uint32_t n_par = 1u << (3 * (level - 1));
-  dim3 grid((n_par + NT - 1) / NT, 8);
-  if (ext)
-    k_m2l_fp32<P, EXT_TOP><<<grid, threads, smem, s>>>(Pl.M[level], Pl.F[level], Pl.tab[level], Pl.tab_lo[level],
-                                                       Pl.offsets[level], Pl.n_off[level], level);
+  const int nsplit = m2l_fp32_splits(Pl, level);
+  const int n_off = Pl.n_off[level];
+  const int per = (n_off + nsplit - 1) / nsplit;
+  const size_t field = ((size_t)1 << (3 * level)) * 4 * P3;
+  // coarse levels write (sum, low part) pairs per offset range, reduced in FP64
+  float* out = ext ? Pl.m2l_part : Pl.F[level];
+  dim3 grid((n_par + NT - 1) / NT, 8, nsplit);
+  if (level == 2)
+    k_m2l_df<P><<<grid, threads, sizeof(float4) * (2 * D * D * D + P3 * (NT / 4)), s>>>(
+        Pl.M[level], out, Pl.tab[level], Pl.tab_lo[level], Pl.offsets[level], n_off, level, per, field, 1);
+  else if (ext)
+    k_m2l_fp32<P, EXT_TOP><<<grid, threads, smem, s>>>(Pl.M[level], out, Pl.tab[level], Pl.tab_lo[level],
+                                                       Pl.offsets[level], n_off, level, per, field, 1);
   else
-    k_m2l_fp32<P, 0><<<grid, threads, smem, s>>>(Pl.M[level], Pl.F[level], Pl.tab[level], nullptr,
-                                                 Pl.offsets[level], Pl.n_off[level], level);
+    k_m2l_fp32<P, 0><<<grid, threads, smem, s>>>(Pl.M[level], out, Pl.tab[level], nullptr, Pl.offsets[level],
+                                                 n_off, level, per, field, 0);
+  if (ext) k_sum_ranges<<<4 * Pl.num_sms, 256, 0, s>>>(Pl.m2l_part, nsplit, field, Pl.F64[level], Pl.F[level]);
   return cudaGetLastError();
 }
 
 template <int P>
 cudaError_t setup_p() {
   constexpr int EXT_TOP = P >= 7 ? 2 : 1;
-  cudaError_t e = cudaFuncSetAttribute(k_m2l_fp32<P, EXT_TOP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_m2l_df<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_m2l_fp32<P, EXT_TOP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_m2l_fp32<P, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 }  // namespace
+
+int m2l_fp32_splits(const Plan& P, int level) {
+  if (level > kExtTopLevel) return 1;     // fine levels have targets enough
+  const int nt = P.p * P.p * P.p > 256 ? 4 : 8;
+  const long ctas = (long)(((1u << (3 * (level - 1))) + nt - 1) / nt) * 8;
+  long want = (2L * P.num_sms + ctas - 1) / ctas;
+  if (want > P.n_off[level]) want = P.n_off[level];
+  return want < 1 ? 1 : (int)want;
+}
 
 cudaError_t setup_m2l_fp32(const Plan& P) {
   switch (P.p) {
