@@ -125,12 +125,14 @@ int fmm_plan_set_m2l_group(fmm_plan* plan, int offsets_per_partial);
 
 /* Mixed-precision forms: the first tree level whose M2L (eq. fmm2) runs on
  * the tensor cores; coarser levels run the FP32 CUDA-core kernel.  Default
- * and minimum 4 (levels 2 and 3 always use the split-table FP32 kernel); a
- * value above the leaf level L keeps every level on the CUDA cores.  At high
- * order (p >= 7) the gridlet masses of non-leaf nodes are large alternating
- * sums (Lagrange extrapolation to the node edges), which BF16 splits round
- * badly; putting only the leaf level (tc_min_level = L) on the tensor cores
- * keeps most of the speed.  FMM_ERR_ARG outside 4..9. */
+ * and minimum 4 (levels 2 and 3 always use the extended-precision CUDA-core
+ * kernels).  A value above the leaf level L keeps every level on the CUDA
+ * cores.  At order >= 7 only the leaf level can run on the tensor cores: the
+ * L2L interpolation to the children extrapolates beyond the parent gridlet
+ * (absolute weight sums ~1100 at p = 8), so every level above the leaves
+ * keeps FP64 local fields fed by compensated CUDA-core sums.  Lowering the
+ * level after the first mixed-precision solve builds the translation tiles
+ * of the new levels (synchronously).  FMM_ERR_ARG outside 4..9. */
 int fmm_plan_set_tc_min_level(fmm_plan* plan, int level);
 
 /* Synchronise the device and read the plan's device error word: FMM_OK, or

@@ -241,7 +241,7 @@ fmm_plan* fmm_plan_create(int N, int L, int order) {
     // scratch for the offset-range partials of the coarse FP32 M2L levels
     size_t part = 0;
     for (int l = 2; l <= L; ++l) {
-      if (l > fmm::kExtTopLevel) continue;
+      if (!fmm::wide_level(*P, l)) continue;
       const int ns = fmm::m2l_fp32_splits(*P, l);
       const size_t need = 2 * (size_t)ns * ((size_t)1 << (3 * l)) * 4 * p3;
       if (need > part) part = need;
@@ -282,21 +282,25 @@ int fmm_plan_get_shape(const fmm_plan* plan, int* N, int* L, int* order, int* S)
 }
 
 namespace {
-// Tensor-core M2L buffers: split tables and split multipoles for every level
-// at or below kTcMinLevel.  Allocated and tabulated once, synchronously.
+// Tensor-core M2L buffers: split tables, split multipoles and the translation
+// tiles of every level from the first tensor-core level down to the leaves
+// (levels that already have them are kept).  Tabulated once, synchronously.
 int prepare_tc(Plan& P) {
-  if (P.tc_ready) return FMM_OK;
   const size_t E = 8 * P.p - 1;
   const size_t kp = (size_t)fmm::tc_padded_k(P.p);
-  for (int l = fmm::kTcMinLevel; l <= P.L; ++l) {
+  bool made = false;
+  for (int l = fmm::tc_first_level(P); l <= P.L; ++l) {
+    if (P.Apre[l]) continue;
     const size_t nodes = (size_t)1 << (3 * l);
-    if (!dev_alloc(&P.tab_bf[l], E * E * E) || cudaMalloc(&P.Mbf_hi[l], nodes * kp * 2 * 2) != cudaSuccess ||
+    if ((!P.tab_bf[l] && !dev_alloc(&P.tab_bf[l], E * E * E)) ||
+        (!P.Mbf_hi[l] && cudaMalloc(&P.Mbf_hi[l], nodes * kp * 2 * 2) != cudaSuccess) ||
         cudaMalloc(&P.Apre[l], fmm::tc_apre_bytes(P.p)) != cudaSuccess)
       return FMM_ERR_ALLOC;
     if (fmm::launch_tab_bf16(P, l, 0) != cudaSuccess || fmm::launch_build_a(P, l, 0) != cudaSuccess)
       return FMM_ERR_CUDA;
+    made = true;
   }
-  if (cudaDeviceSynchronize() != cudaSuccess) return FMM_ERR_CUDA;
+  if (made && cudaDeviceSynchronize() != cudaSuccess) return FMM_ERR_CUDA;
   P.tc_ready = 1;
   return FMM_OK;
 }
@@ -334,7 +338,12 @@ int fmm_plan_set_m2l_group(fmm_plan* plan, int offsets_per_partial) {
 
 int fmm_plan_set_tc_min_level(fmm_plan* plan, int level) {
   if (!plan || level < fmm::kTcMinLevel || level > fmm::kMaxLevel + 1) return set_err(FMM_ERR_ARG);
-  reinterpret_cast<Plan*>(plan)->tc_min_level = level;
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  P.tc_min_level = level;
+  if (P.tc_ready) {   // a lower first level needs its tiles now
+    const int rc = prepare_tc(P);
+    if (rc != FMM_OK) return set_err(rc);
+  }
   return set_err(FMM_OK);
 }
 
@@ -359,6 +368,7 @@ int fmm_plan_set_correction(fmm_plan* plan, const float* weights, size_t n) {
   FMM_CUDA_TRY(fmm::launch_tables(P, 0));
   if (P.tc_ready) {
     for (int l = fmm::kTcMinLevel; l <= P.L; ++l) {
+      if (!P.Apre[l]) continue;
       FMM_CUDA_TRY(fmm::launch_tab_bf16(P, l, 0));
       FMM_CUDA_TRY(fmm::launch_build_a(P, l, 0));
     }
@@ -469,7 +479,7 @@ int fmm_solve(fmm_plan* plan, const float* density, float* potential, float* acc
   const bool tc = P.prec != FMM_PREC_FP32 && P.tc_ready;
   for (int l = 2; l <= P.L; ++l) {
     FMM_CUDA_TRY(mark(FMM_TIME_M2L_LEVEL0 + l, 0));
-    if (tc && l >= P.tc_min_level) {
+    if (tc && l >= fmm::tc_first_level(P)) {
       FMM_CUDA_TRY(fmm::launch_split_bf16(P, l, s));
       FMM_CUDA_TRY(fmm::launch_m2l_tc(P, l, P.prec, s));
     } else {

@@ -36,7 +36,8 @@ __global__ void k_l2l(const float* __restrict__ Fp, int p, const float2* __restr
   }
 }
 
-// FP64 variant for parents at the coarse levels (<= kExtTopLevel), one field
+// FP64 variant for parents at the wide levels (the coarse levels 2 and 3; at
+// order >= 7 every level above the leaves), one field
 // at a time (shared memory).  The child field is F64 (a coarse child, whose
 // FP32 copy is refreshed too) or the FP32 field of the first fine level, to
 // which the FP64 contribution is added before a single rounding.
@@ -86,9 +87,9 @@ cudaError_t launch_l2l(Plan& P, int level, cudaStream_t s) {
   const int p = P.p, K = 2 * p, p3 = p * p * p;
   const size_t smem = sizeof(float2) * p * K + sizeof(float) * (4 * p3 + 4 * p * p * K + 4 * p * K * K + 4 * K * K * K);
   const unsigned parents = 1u << (3 * level);
-  if (level <= kExtTopLevel) {
+  if (wide_level(P, level)) {
     const size_t smem64 = sizeof(double) * (p * K + p3 + p * p * K + p * K * K + K * K * K);
-    k_l2l64<<<parents, 256, smem64, s>>>(P.F64[level], p, P.wd_m2m, level + 1 <= kExtTopLevel ? P.F64[level + 1] : nullptr,
+    k_l2l64<<<parents, 256, smem64, s>>>(P.F64[level], p, P.wd_m2m, wide_level(P, level + 1) ? P.F64[level + 1] : nullptr,
                                          P.F[level + 1]);
     return cudaGetLastError();
   }

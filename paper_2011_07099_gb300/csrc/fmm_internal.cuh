@@ -52,6 +52,12 @@ __host__ __device__ inline void unmorton(uint32_t k, uint32_t& x, uint32_t& y, u
   z = compact3(k >> 2);
 }
 
+// At high order the downward interpolation amplifies the rounding of the
+// local fields much more (absolute L2L weight sums ~1100 at p = 8 against ~160
+// at p = 6), so from this order on every level above the leaves keeps FP64
+// local fields, and the tensor cores take only the leaf level.
+constexpr int kWideOrder = 7;
+
 // ------------------------------------------------------------------- the plan
 struct Plan {
   int N = 0, L = 0, p = 0, S = 0;
@@ -67,7 +73,7 @@ struct Plan {
   float* M[kMaxLevel + 1] = {};     // gridlet masses, 8^l x p^3, levels 2..L
   float* F[kMaxLevel + 1] = {};     // local fields, 8^l x 4 x p^3, levels 2..L
   float* m2l_part = nullptr;        // coarse FP32 M2L levels: ranges x (sum, low part) x 8^l x 4 p^3
-  // Local fields of the levels <= kExtTopLevel in FP64: the L2L interpolation
+  // Local fields of the wide levels in FP64: the L2L interpolation
   // to the children extrapolates to points outside the parent's gridlet
   // (weights up to ~160 in absolute sum at p = 6), so FP32 storage of the
   // coarse local fields would cost ~1e-6 of the potential.
@@ -117,6 +123,15 @@ struct Plan {
 // Opt-in shared-memory limits (and other function attributes) are set once at
 // plan creation, never inside a solve, so a solve is safe to capture.
 cudaError_t setup_upward(const Plan& P);
+// Levels whose local field is kept in FP64 (M2L output reduced in FP64, L2L
+// from them in FP64): the two coarse levels, and at high order every level
+// above the leaves.
+inline bool wide_level(const Plan& P, int l) { return l <= kExtTopLevel || (P.p >= kWideOrder && l < P.L); }
+// First level of the tensor-core M2L in the mixed forms.
+inline int tc_first_level(const Plan& P) {
+  return P.p >= kWideOrder ? (P.tc_min_level > P.L ? P.tc_min_level : P.L) : P.tc_min_level;
+}
+
 cudaError_t setup_m2l_fp32(const Plan& P);
 // Number of offset ranges the FP32 M2L of a level is split into (1 = none).
 int m2l_fp32_splits(const Plan& P, int level);

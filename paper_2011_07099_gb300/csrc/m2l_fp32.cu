@@ -343,7 +343,8 @@ cudaError_t launch_p(Plan& Pl, int level, cudaStream_t s) {
   constexpr int NT = M2LShape<P>::NT;
   constexpr int EXT_TOP = P >= 7 ? 2 : 1;
   const int threads = M2LShape<P>::THREADS;
-  const bool ext = level <= kExtTopLevel;
+  const bool ext = level <= kExtTopLevel;          // split table
+  const bool wide = wide_level(Pl, level);         // (sum, low part) outputs reduced in FP64
   const size_t lo_bytes = ext ? (EXT_TOP == 2 ? sizeof(float4) : sizeof(float)) * D * D * D : 0;
   const size_t smem = sizeof(float4) * (D * D * D + P3 * (NT / 4)) + lo_bytes;
   const uint32_t n_par = 1u << (3 * (level - 1));
@@ -351,8 +352,8 @@ cudaError_t launch_p(Plan& Pl, int level, cudaStream_t s) {
   const int n_off = Pl.n_off[level];
   const int per = (n_off + nsplit - 1) / nsplit;
   const size_t field = ((size_t)1 << (3 * level)) * 4 * P3;
-  // coarse levels write (sum, low part) pairs per offset range, reduced in FP64
-  float* out = ext ? Pl.m2l_part : Pl.F[level];
+  // wide levels write (sum, low part) pairs per offset range, reduced in FP64
+  float* out = wide ? Pl.m2l_part : Pl.F[level];
   dim3 grid((n_par + NT - 1) / NT, 8, nsplit);
   if (level == 2)
     k_m2l_df<P><<<grid, threads, sizeof(float4) * (2 * D * D * D + P3 * (NT / 4)), s>>>(
@@ -362,8 +363,8 @@ cudaError_t launch_p(Plan& Pl, int level, cudaStream_t s) {
                                                        Pl.offsets[level], n_off, level, per, field, 1);
   else
     k_m2l_fp32<P, 0><<<grid, threads, smem, s>>>(Pl.M[level], out, Pl.tab[level], nullptr, Pl.offsets[level],
-                                                 n_off, level, per, field, 0);
-  if (ext) k_sum_ranges<<<4 * Pl.num_sms, 256, 0, s>>>(Pl.m2l_part, nsplit, field, Pl.F64[level], Pl.F[level]);
+                                                 n_off, level, per, field, wide ? 1 : 0);
+  if (wide) k_sum_ranges<<<4 * Pl.num_sms, 256, 0, s>>>(Pl.m2l_part, nsplit, field, Pl.F64[level], Pl.F[level]);
   return cudaGetLastError();
 }
 

@@ -67,7 +67,8 @@ def test_autotuner_picks_a_valid_level_and_caches_it(B, tmp_path):
     lines = open(cache).read().strip().splitlines()
     assert len(lines) == 1 and '"L": %d' % L in lines[0]
     L2, ms2 = B.fmm_autotune_levels(64, 4, B.FMM_PREC_BF16X3, cache)
-    assert (L2, round(ms2, 3)) == (L, round(ms, 3))
+    # the cache keeps the time with a few significant digits
+    assert L2 == L and ms2 == pytest.approx(ms, rel=1e-3)
     assert len(open(cache).read().strip().splitlines()) == 1      # served from the cache
 
 
