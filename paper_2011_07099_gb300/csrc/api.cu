@@ -98,6 +98,7 @@ void free_plan(Plan* P) {
     cudaFree(P->tab[l]);
     cudaFree(P->tab_lo[l]);
     cudaFree(P->F64[l]);
+    cudaFree(P->M64[l]);
     cudaFree(P->offsets[l]);
   }
   cudaFree(P->near_tab);
@@ -191,7 +192,9 @@ fmm_plan* fmm_plan_create(int N, int L, int order) {
     const size_t E = 8 * p - 1;
     ok = dev_alloc(&P->M[l], nodes * p3) && dev_alloc(&P->F[l], nodes * 4 * p3) &&
          dev_alloc(&P->tab[l], E * E * E);
-    if (ok && l <= fmm::kExtTopLevel) ok = dev_alloc(&P->tab_lo[l], E * E * E);
+    // split tables for the coarse levels, and for every wide level of the high orders
+    if (ok && (l <= fmm::kExtTopLevel || (p >= fmm::kWideOrder && l < L))) ok = dev_alloc(&P->tab_lo[l], E * E * E);
+    if (ok && p >= fmm::kWideOrder && l < L) ok = dev_alloc(&P->M64[l], nodes * p3);
   }
   ok = ok && dev_alloc(&P->near_tab, (size_t)8 * S * S * S) && dev_alloc(&P->w_p2m, (size_t)p * S) &&
        dev_alloc(&P->w_m2m, (size_t)p * 2 * p) && dev_alloc(&P->wd_p2m, (size_t)p * S) &&

@@ -78,6 +78,9 @@ struct Plan {
   // (weights up to ~160 in absolute sum at p = 6), so FP32 storage of the
   // coarse local fields would cost ~1e-6 of the potential.
   double* F64[kMaxLevel + 1] = {};
+  // At order >= kWideOrder the gridlet masses of the wide levels are kept in
+  // FP64 as well (M2M writes both copies; M2L reads them as hi + lo).
+  double* M64[kMaxLevel + 1] = {};
   float4* tab[kMaxLevel + 1] = {};  // (G, -dG/dx, -dG/dy, -dG/dz) at n dx_l, n in [-(4p-1), 4p-1]^3
   float4* tab_lo[kMaxLevel + 1] = {};  // v - fl32(v) of the same entries, 4 fields (levels 2..kExtTopLevel)
   float4* near_tab = nullptr;       // the same at cell spacing for |d_i| in [0, 2S-1], folded

@@ -43,12 +43,14 @@ struct M2LShape {
 };
 
 // EXT: 0 = FP32 table; 1 = the potential also takes G_lo; 2 = all four fields
-// take their low halves.
+// take their low halves; 3 = as 2, and the gridlet masses are read from their
+// FP64 copy as hi + lo (the wide levels of high orders, whose masses are
+// large alternating sums).
 template <int P, int EXT>
 __global__ void __launch_bounds__(M2LShape<P>::THREADS)
 k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __restrict__ tab,
            const float4* __restrict__ tab_lo, const int8_t* __restrict__ offs, int n_off, int level,
-           int per_split, size_t split_stride, int pairs) {
+           int per_split, size_t split_stride, int pairs, const double* __restrict__ M64) {
   constexpr int P3 = P * P * P;
   constexpr int NT = M2LShape<P>::NT;
   constexpr int D = 2 * P - 1;          // table window per dimension
@@ -58,7 +60,8 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
   float4* win = sm4;                                     // D3 float4
   float4* msrc = win + D3;                               // P3 x (NT/4) float4: [s][k]
   float* win_lo = reinterpret_cast<float*>(msrc + P3 * (NT / 4));   // D3 floats (EXT == 1)
-  float4* win_lo4 = msrc + P3 * (NT / 4);                            // D3 float4 (EXT == 2)
+  float4* win_lo4 = msrc + P3 * (NT / 4);                            // D3 float4 (EXT >= 2)
+  float4* msrc_lo = win_lo4 + D3;                                    // P3 x (NT/4) float4 (EXT == 3)
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int ctype = blockIdx.y;
   const int n = 1 << level;
@@ -97,22 +100,31 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
       const int nx = ox * P + dx + HW, ny = oy * P + dy + HW, nz = oz * P + dz + HW;
       win[i] = __ldg(tab + ((size_t)nz * E + ny) * E + nx);
       if (EXT == 1) win_lo[i] = __ldg(&tab_lo[((size_t)nz * E + ny) * E + nx].x);
-      if (EXT == 2) win_lo4[i] = __ldg(tab_lo + ((size_t)nz * E + ny) * E + nx);
+      if (EXT >= 2) win_lo4[i] = __ldg(tab_lo + ((size_t)nz * E + ny) * E + nx);
     }
     float* ms = reinterpret_cast<float*>(msrc);
+    float* ms_lo = reinterpret_cast<float*>(msrc_lo);
     for (int i = tid; i < NT * P3; i += nthr) {
       const int k = i / P3, s = i % P3;
-      float v = 0.f;
+      float v = 0.f, vlo = 0.f;
       if (par0 + k < n_par) {
         const uint32_t sx = (uint32_t)(tx[k] - ox) & (n - 1), sy = (uint32_t)(ty[k] - oy) & (n - 1),
                        sz = (uint32_t)(tz[k] - oz) & (n - 1);
-        v = __ldg(M + (size_t)morton(sx, sy, sz) * P3 + s);
+        const size_t g = (size_t)morton(sx, sy, sz) * P3 + s;
+        if (EXT == 3) {
+          const double d = __ldg(M64 + g);
+          v = (float)d;
+          vlo = (float)(d - (double)v);
+        } else {
+          v = __ldg(M + g);
+        }
       }
       ms[s * NT + k] = v;
+      if (EXT == 3) ms_lo[s * NT + k] = vlo;
     }
     __syncthreads();
     if (r < P3) {
-      constexpr int NLO = EXT == 2 ? 4 : 1;
+      constexpr int NLO = EXT >= 2 ? 4 : 1;
       float plo[NLO][NT];
 #pragma unroll
       for (int f = 0; f < NLO; ++f)
@@ -137,12 +149,15 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
             const int s = (sz * P + sy) * P + sx;
             const int w = rbase - ((sz * D + sy) * D + sx);
             const float4 t = win[w];
-            const float4 tl = EXT == 2 ? win_lo4[w] : make_float4(EXT == 1 ? win_lo[w] : 0.f, 0.f, 0.f, 0.f);
+            const float4 tl = EXT >= 2 ? win_lo4[w] : make_float4(EXT == 1 ? win_lo[w] : 0.f, 0.f, 0.f, 0.f);
             const float4* mv = msrc + s * (NT / 4);
+            const float4* mvl = msrc_lo + s * (NT / 4);
 #pragma unroll
             for (int q = 0; q < NT / 4; ++q) {
               const float4 m = mv[q];
               const float mm[4] = {m.x, m.y, m.z, m.w};
+              const float4 ml = EXT == 3 ? mvl[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+              const float mml[4] = {ml.x, ml.y, ml.z, ml.w};
 #pragma unroll
               for (int j = 0; j < 4; ++j) {
                 row[0][4 * q + j] = fmaf(t.x, mm[j], row[0][4 * q + j]);
@@ -150,10 +165,16 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
                 row[2][4 * q + j] = fmaf(t.z, mm[j], row[2][4 * q + j]);
                 row[3][4 * q + j] = fmaf(t.w, mm[j], row[3][4 * q + j]);
                 if (EXT >= 1) plo[0][4 * q + j] = fmaf(tl.x, mm[j], plo[0][4 * q + j]);
-                if (EXT == 2) {
+                if (EXT >= 2) {
                   plo[NLO - 3][4 * q + j] = fmaf(tl.y, mm[j], plo[NLO - 3][4 * q + j]);
                   plo[NLO - 2][4 * q + j] = fmaf(tl.z, mm[j], plo[NLO - 2][4 * q + j]);
                   plo[NLO - 1][4 * q + j] = fmaf(tl.w, mm[j], plo[NLO - 1][4 * q + j]);
+                }
+                if (EXT == 3) {
+                  plo[0][4 * q + j] = fmaf(t.x, mml[j], plo[0][4 * q + j]);
+                  plo[NLO - 3][4 * q + j] = fmaf(t.y, mml[j], plo[NLO - 3][4 * q + j]);
+                  plo[NLO - 2][4 * q + j] = fmaf(t.z, mml[j], plo[NLO - 2][4 * q + j]);
+                  plo[NLO - 1][4 * q + j] = fmaf(t.w, mml[j], plo[NLO - 1][4 * q + j]);
                 }
               }
             }
@@ -212,7 +233,7 @@ template <int P>
 __global__ void __launch_bounds__(M2LShape<P>::THREADS)
 k_m2l_df(const float* __restrict__ M, float* __restrict__ F, const float4* __restrict__ tab,
          const float4* __restrict__ tab_lo, const int8_t* __restrict__ offs, int n_off, int level, int per_split,
-         size_t split_stride, int pairs) {
+         size_t split_stride, int pairs, const double* __restrict__ M64) {
   constexpr int P3 = P * P * P;
   constexpr int NT = M2LShape<P>::NT;
   constexpr int D = 2 * P - 1;
@@ -222,6 +243,7 @@ k_m2l_df(const float* __restrict__ M, float* __restrict__ F, const float4* __res
   float4* win = sm4;                       // D3
   float4* wlo = win + D3;                  // D3
   float4* msrc = wlo + D3;                 // P3 x (NT/4): [s][k]
+  float4* mlo4 = msrc + P3 * (NT / 4);     // low halves of FP64 masses (M64 given)
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int ctype = blockIdx.y;
   const int n = 1 << level;
@@ -259,15 +281,24 @@ k_m2l_df(const float* __restrict__ M, float* __restrict__ F, const float4* __res
       wlo[i] = __ldg(tab_lo + g);
     }
     float* ms = reinterpret_cast<float*>(msrc);
+    float* msl = reinterpret_cast<float*>(mlo4);
     for (int i = tid; i < NT * P3; i += nthr) {
       const int k = i / P3, s = i % P3;
-      float v = 0.f;
+      float v = 0.f, vlo = 0.f;
       if (par0 + k < n_par) {
         const uint32_t sx = (uint32_t)(tx[k] - ox) & (n - 1), sy = (uint32_t)(ty[k] - oy) & (n - 1),
                        sz = (uint32_t)(tz[k] - oz) & (n - 1);
-        v = __ldg(M + (size_t)morton(sx, sy, sz) * P3 + s);
+        const size_t g = (size_t)morton(sx, sy, sz) * P3 + s;
+        if (M64) {
+          const double d = __ldg(M64 + g);
+          v = (float)d;
+          vlo = (float)(d - (double)v);
+        } else {
+          v = __ldg(M + g);
+        }
       }
       ms[s * NT + k] = v;
+      if (M64) msl[s * NT + k] = vlo;
     }
     __syncthreads();
     if (r < P3) {
@@ -286,6 +317,8 @@ k_m2l_df(const float* __restrict__ M, float* __restrict__ F, const float4* __res
             for (int q = 0; q < NT / 4; ++q) {
               const float4 m4 = mv[q];
               const float mm[4] = {m4.x, m4.y, m4.z, m4.w};
+              const float4 l4 = M64 ? mlo4[s * (NT / 4) + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+              const float ml[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
               for (int j = 0; j < 4; ++j) {
                 const int k = 4 * q + j;
@@ -298,7 +331,7 @@ k_m2l_df(const float* __restrict__ M, float* __restrict__ F, const float4* __res
                   const float z = __fsub_rn(t, hs[f][k]);
                   const float se = __fadd_rn(__fsub_rn(hs[f][k], __fsub_rn(t, z)), __fsub_rn(pr, z));
                   hs[f][k] = t;
-                  lc[f][k] = fmaf(gl[f], mm[j], __fadd_rn(lc[f][k], __fadd_rn(pe, se)));
+                  lc[f][k] = fmaf(gh[f], ml[j], fmaf(gl[f], mm[j], __fadd_rn(lc[f][k], __fadd_rn(pe, se))));
                 }
               }
             }
@@ -355,15 +388,19 @@ cudaError_t launch_p(Plan& Pl, int level, cudaStream_t s) {
   // wide levels write (sum, low part) pairs per offset range, reduced in FP64
   float* out = wide ? Pl.m2l_part : Pl.F[level];
   dim3 grid((n_par + NT - 1) / NT, 8, nsplit);
+  const double* m64 = Pl.M64[level];      // FP64 masses: wide levels of the high orders
   if (level == 2)
-    k_m2l_df<P><<<grid, threads, sizeof(float4) * (2 * D * D * D + P3 * (NT / 4)), s>>>(
-        Pl.M[level], out, Pl.tab[level], Pl.tab_lo[level], Pl.offsets[level], n_off, level, per, field, 1);
+    k_m2l_df<P><<<grid, threads, sizeof(float4) * (2 * D * D * D + 2 * P3 * (NT / 4)), s>>>(
+        Pl.M[level], out, Pl.tab[level], Pl.tab_lo[level], Pl.offsets[level], n_off, level, per, field, 1, m64);
+  else if (m64)
+    k_m2l_fp32<P, 3><<<grid, threads, sizeof(float4) * (2 * D * D * D + 2 * P3 * (NT / 4)), s>>>(
+        Pl.M[level], out, Pl.tab[level], Pl.tab_lo[level], Pl.offsets[level], n_off, level, per, field, 1, m64);
   else if (ext)
     k_m2l_fp32<P, EXT_TOP><<<grid, threads, smem, s>>>(Pl.M[level], out, Pl.tab[level], Pl.tab_lo[level],
-                                                       Pl.offsets[level], n_off, level, per, field, 1);
+                                                       Pl.offsets[level], n_off, level, per, field, 1, nullptr);
   else
     k_m2l_fp32<P, 0><<<grid, threads, smem, s>>>(Pl.M[level], out, Pl.tab[level], nullptr, Pl.offsets[level],
-                                                 n_off, level, per, field, wide ? 1 : 0);
+                                                 n_off, level, per, field, wide ? 1 : 0, nullptr);
   if (wide) k_sum_ranges<<<4 * Pl.num_sms, 256, 0, s>>>(Pl.m2l_part, nsplit, field, Pl.F64[level], Pl.F[level]);
   return cudaGetLastError();
 }
@@ -372,6 +409,8 @@ template <int P>
 cudaError_t setup_p() {
   constexpr int EXT_TOP = P >= 7 ? 2 : 1;
   cudaError_t e = cudaFuncSetAttribute(k_m2l_df<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_m2l_fp32<P, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_m2l_fp32<P, EXT_TOP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;

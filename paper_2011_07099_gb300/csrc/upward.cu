@@ -76,7 +76,10 @@ __global__ void k_p2m(const float* __restrict__ rho, const double* __restrict__ 
 
 // a4: one CTA per parent; the 8 children (keys 8P + c) are gathered into a
 // (2p)^3 mesh and contracted with the [p][2p] Lagrange matrix on each axis.
-__global__ void k_m2m(const float* __restrict__ Mc, int p, const double* __restrict__ w, float* __restrict__ Mp) {
+// At high order the FP64 copies are read (Mc64, when the children keep one)
+// and written (Mp64) as well.
+__global__ void k_m2m(const float* __restrict__ Mc, const double* __restrict__ Mc64, int p,
+                      const double* __restrict__ w, float* __restrict__ Mp, double* __restrict__ Mp64) {
   extern __shared__ double smd[];
   const int K = 2 * p, p3 = p * p * p;
   double* W = smd;              // p*K
@@ -91,11 +94,14 @@ __global__ void k_m2m(const float* __restrict__ Mc, int p, const double* __restr
     const int c = i / p3, q = i % p3;
     const int qx = q % p, qy = (q / p) % p, qz = q / (p * p);
     const int ux = (c & 1) * p + qx, uy = ((c >> 1) & 1) * p + qy, uz = (c >> 2) * p + qz;
-    in[(uz * K + uy) * K + ux] = (double)src[i];
+    in[(uz * K + uy) * K + ux] = Mc64 ? Mc64[(size_t)blockIdx.x * 8 * p3 + i] : (double)src[i];
   }
   __syncthreads();
   contract3_d(in, t1, t2, out, K, p, W, K, tid, nthr);
-  for (int i = tid; i < p3; i += nthr) Mp[(size_t)blockIdx.x * p3 + i] = (float)out[i];
+  for (int i = tid; i < p3; i += nthr) {
+    Mp[(size_t)blockIdx.x * p3 + i] = (float)out[i];
+    if (Mp64) Mp64[(size_t)blockIdx.x * p3 + i] = out[i];
+  }
 }
 
 }  // namespace
@@ -125,7 +131,7 @@ cudaError_t launch_m2m(Plan& P, int level, cudaStream_t s) {
   const int p = P.p, K = 2 * p;
   const size_t smem = sizeof(double) * (p * K + K * K * K + K * K * p + K * p * p + p * p * p);
   const unsigned parents = 1u << (3 * level);
-  k_m2m<<<parents, 128, smem, s>>>(P.M[level + 1], p, P.wd_m2m, P.M[level]);
+  k_m2m<<<parents, 128, smem, s>>>(P.M[level + 1], P.M64[level + 1], p, P.wd_m2m, P.M[level], P.M64[level]);
   return cudaGetLastError();
 }
 
