@@ -194,7 +194,10 @@ fmm_plan* fmm_plan_create(int N, int L, int order) {
          dev_alloc(&P->tab[l], E * E * E);
     // split tables for the coarse levels, and for every wide level of the high orders
     if (ok && (l <= fmm::kExtTopLevel || (p >= fmm::kWideOrder && l < L))) ok = dev_alloc(&P->tab_lo[l], E * E * E);
-    if (ok && p >= fmm::kWideOrder && l < L) ok = dev_alloc(&P->M64[l], nodes * p3);
+    // FP64 gridlet masses at every level at high order (the leaf copy feeds M2M:
+    // the coarse far-field sums cancel ~1000-fold there, so FP32 rounding of
+    // the leaf masses alone would cost ~1e-6)
+    if (ok && p >= fmm::kWideOrder) ok = dev_alloc(&P->M64[l], nodes * p3);
   }
   ok = ok && dev_alloc(&P->near_tab, (size_t)8 * S * S * S) && dev_alloc(&P->w_p2m, (size_t)p * S) &&
        dev_alloc(&P->w_m2m, (size_t)p * 2 * p) && dev_alloc(&P->wd_p2m, (size_t)p * S) &&

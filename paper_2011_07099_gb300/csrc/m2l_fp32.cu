@@ -223,7 +223,9 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
 
 // Level 2 (the first far-field level, 37 periodic interaction nodes, Sec. 2)
 // carries the long-range potential: its terms are ~100 times larger than the
-// potential they sum to, so FP32 products alone cost ~1e-6.  This kernel sums
+// potential they sum to, so FP32 products alone cost ~1e-6.  At order 8 on
+// point-like clumps the cancellation reaches ~1000-fold at every level, so
+// there every level above the leaves uses this kernel.  This kernel sums
 // eq. fmm2 there in double-float arithmetic: every product with the split
 // table value G_hi + G_lo is accumulated as an unevaluated sum (s, c) with
 // error-free transformations (TwoProd by FMA, TwoSum; Ogita, Rump and Oishi,
@@ -388,8 +390,8 @@ cudaError_t launch_p(Plan& Pl, int level, cudaStream_t s) {
   // wide levels write (sum, low part) pairs per offset range, reduced in FP64
   float* out = wide ? Pl.m2l_part : Pl.F[level];
   dim3 grid((n_par + NT - 1) / NT, 8, nsplit);
-  const double* m64 = Pl.M64[level];      // FP64 masses: wide levels of the high orders
-  if (level == 2)
+  const double* m64 = wide ? Pl.M64[level] : nullptr;   // FP64 masses: wide levels of the high orders
+  if (level == 2 || m64)   // double-float sums: level 2, and every wide level of the high orders
     k_m2l_df<P><<<grid, threads, sizeof(float4) * (2 * D * D * D + 2 * P3 * (NT / 4)), s>>>(
         Pl.M[level], out, Pl.tab[level], Pl.tab_lo[level], Pl.offsets[level], n_off, level, per, field, 1, m64);
   else if (m64)

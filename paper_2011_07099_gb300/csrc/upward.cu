@@ -50,7 +50,7 @@ __global__ void k_final_mean(const double* __restrict__ partials, int n, double 
 // m = (rho - mean) / N^3 and the contraction are FP64; the gridlet masses are
 // rounded once to FP32.
 __global__ void k_p2m(const float* __restrict__ rho, const double* __restrict__ mean, int N, int S, int p,
-                      const double* __restrict__ w, float* __restrict__ Mout) {
+                      const double* __restrict__ w, float* __restrict__ Mout, double* __restrict__ Mout64) {
   extern __shared__ double smd[];
   double* W = smd;                     // p*S
   double* in = W + p * S;              // S^3
@@ -71,7 +71,10 @@ __global__ void k_p2m(const float* __restrict__ rho, const double* __restrict__ 
   __syncthreads();
   contract3_d(in, t1, t2, out, S, p, W, S, tid, nthr);
   const int p3 = p * p * p;
-  for (int i = tid; i < p3; i += nthr) Mout[(size_t)blockIdx.x * p3 + i] = (float)out[i];
+  for (int i = tid; i < p3; i += nthr) {
+    Mout[(size_t)blockIdx.x * p3 + i] = (float)out[i];
+    if (Mout64) Mout64[(size_t)blockIdx.x * p3 + i] = out[i];
+  }
 }
 
 // a4: one CTA per parent; the 8 children (keys 8P + c) are gathered into a
@@ -123,7 +126,7 @@ cudaError_t launch_p2m(Plan& P, const float* rho, cudaStream_t s) {
   const int S = P.S, p = P.p;
   const size_t smem = sizeof(double) * (p * S + S * S * S + S * S * p + S * p * p + p * p * p);
   const unsigned leaves = 1u << (3 * P.L);
-  k_p2m<<<leaves, 128, smem, s>>>(rho, P.d_mean, P.N, S, p, P.wd_p2m, P.M[P.L]);
+  k_p2m<<<leaves, 128, smem, s>>>(rho, P.d_mean, P.N, S, p, P.wd_p2m, P.M[P.L], P.M64[P.L]);
   return cudaGetLastError();
 }
 

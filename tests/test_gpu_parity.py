@@ -159,29 +159,10 @@ FULL = [
     (256, 5, 6, 5, [[0, 0, 0], [31, 31, 31], [5, 17, 30]]),
     (128, 5, 4, 1, [[0, 0, 0], [31, 31, 31], [7, 20, 13]]),
     # the clustered order-8 recipe (1 + lognormal sigma 1.5 + Plummer clumps)
-    # at 256^3, S = p = 8: the high-order precision path (FP64 local fields
-    # above the leaves)
-    pytest.param(256, 5, 8, 4, [[1, 2, 3], [15, 0, 31]], marks=pytest.mark.xfail(
-        reason="order 8 on point-like clumps: FP32 path at ~3e-5 of the oracle (known gap)", strict=False)),
+    # at 256^3, S = p = 8: the high-order precision path (FP64 masses and
+    # local fields, double-float M2L at every level above the leaves)
+    (256, 5, 8, 4, [[1, 2, 3], [15, 0, 31]]),
 ]
-
-
-def test_order8_clustered_sampled_leaves_within_stated_bound(B):
-    # the order-8 clustered workload at 256^3 (S = p = 8): the plain FP32 form
-    # is not yet within 1e-6 of the oracle there (gridlet masses of point-like
-    # clump cores are large alternating sums); the bound it meets is stated
-    N, L, p, leaves = 256, 5, 8, np.array([[1, 2, 3], [15, 0, 31]])
-    rho = inputs.config_density_torch(4, torch.device("cuda", 0), n=N).cpu().numpy()
-    plan, phi, acc = _gpu_solve(B, rho, L, p)
-    ref = ofmm.solve_at(rho, L, p, leaves)
-    S = N >> L
-    g = np.concatenate([phi[None], acc])
-    got = np.stack([g[:, a * S:(a + 1) * S, b * S:(b + 1) * S, c * S:(c + 1) * S].reshape(4, -1)
-                    for a, b, c in leaves])
-    e_phi, e_g = _rel(got[:, 0], ref[:, 0]), _rel(got[:, 1:], ref[:, 1:])
-    print(f"order 8 clustered vs oracle: phi {e_phi:.3e} g {e_g:.3e}")
-    assert e_phi <= 1e-4 and e_g <= 1e-4
-    plan.close()
 
 
 @pytest.mark.parametrize("N,L,p,cfg,leaves", FULL)

@@ -85,9 +85,14 @@ def test_bf16_matches_oracle(B):
 @pytest.mark.parametrize("N,L,p,cfg,leaves", [
     (256, 5, 6, 5, [[0, 0, 0], [31, 31, 31], [5, 17, 30]]),
     (128, 5, 4, 1, [[0, 0, 0], [31, 31, 31], [7, 20, 13]]),
+    # order 8, clustered recipe: only the leaf level runs on the tensor cores
+    (256, 5, 8, 4, [[1, 2, 3], [15, 0, 31]]),
 ])
 def test_bf16x3_full_size_sampled(B, N, L, p, cfg, leaves):
-    rho = inputs.config_density(cfg, n=N)
+    if cfg == 4:   # the clump recipe is evaluated on the device (4096 clumps)
+        rho = inputs.config_density_torch(cfg, torch.device("cuda", 0), n=N).cpu().numpy()
+    else:
+        rho = inputs.config_density(cfg, n=N)
     phi, acc = _solve(B, rho, L, p, B.FMM_PREC_BF16X3)
     leaves = np.array(leaves)
     ref = ofmm.solve_at(rho, L, p, leaves)
