@@ -134,9 +134,9 @@ k_p2p(const float* __restrict__ rho, const double* __restrict__ mean, int N, int
     const int row = tid % ROWS, zg = tid / ROWS;
     const int cz = row / S, cy = row % S;
     float a[4][S];
-  #pragma unroll
+#pragma unroll
     for (int f = 0; f < 4; ++f)
-  #pragma unroll
+#pragma unroll
       for (int x = 0; x < S; ++x) a[f][x] = 0.f;
 
     // Rounding: each source row's 3S terms go into a fresh row partial, rows into
@@ -149,49 +149,54 @@ k_p2p(const float* __restrict__ rho, const double* __restrict__ mean, int N, int
         const int adz = dz < 0 ? -dz : dz;
         const float sz = dz > 0 ? 1.f : (dz < 0 ? -1.f : 0.f);
         float pl[4][S];
-  #pragma unroll
+#pragma unroll
         for (int f = 0; f < 4; ++f)
-  #pragma unroll
+#pragma unroll
           for (int x = 0; x < S; ++x) pl[f][x] = 0.f;
-  #pragma unroll 1
+#pragma unroll 1
         for (int yp = 0; yp < W; ++yp) {
           const int dy = cy + S - yp;
           const int ady = dy < 0 ? -dy : dy;
           const float sy = dy > 0 ? 1.f : (dy < 0 ? -1.f : 0.f);
           const float4* trow = tab + (adz * TD + ady) * TS;
           float4 t[TD];
-  #pragma unroll
+#pragma unroll
           for (int j = 0; j < TD; ++j) t[j] = trow[j];
           const float* mrow = win + (zp * W + yp) * W;
           float rw[4][S];
-  #pragma unroll
+#pragma unroll
           for (int f = 0; f < 4; ++f)
-  #pragma unroll
+#pragma unroll
             for (int x = 0; x < S; ++x) rw[f][x] = 0.f;
-  #pragma unroll
+#pragma unroll
           for (int xp = 0; xp < W; ++xp) {
             const float m = mrow[xp];
-            const float my = sy * m, mz = sz * m;
-  #pragma unroll
+#pragma unroll
             for (int x = 0; x < S; ++x) {
               const int dx = x + S - xp;                    // compile-time after unrolling
               const int adx = dx < 0 ? -dx : dx;
               const float4 v = t[adx];
               rw[0][x] = fmaf(v.x, m, rw[0][x]);
               rw[1][x] = dx >= 0 ? fmaf(v.y, m, rw[1][x]) : fmaf(-v.y, m, rw[1][x]);
-              rw[2][x] = fmaf(v.z, my, rw[2][x]);
-              rw[3][x] = fmaf(v.w, mz, rw[3][x]);
+              rw[2][x] = fmaf(v.z, m, rw[2][x]);            // sign of dy applied per row
+              rw[3][x] = fmaf(v.w, m, rw[3][x]);            // sign of dz applied per plane
             }
           }
-  #pragma unroll
-          for (int f = 0; f < 4; ++f)
-  #pragma unroll
-            for (int x = 0; x < S; ++x) pl[f][x] += rw[f][x];
+#pragma unroll
+          for (int x = 0; x < S; ++x) {
+            pl[0][x] += rw[0][x];
+            pl[1][x] += rw[1][x];
+            pl[2][x] = fmaf(sy, rw[2][x], pl[2][x]);       // sy in {-1, 0, 1}: exact
+            pl[3][x] += rw[3][x];
+          }
         }
-  #pragma unroll
-        for (int f = 0; f < 4; ++f)
-  #pragma unroll
-          for (int x = 0; x < S; ++x) a[f][x] += pl[f][x];
+#pragma unroll
+        for (int x = 0; x < S; ++x) {
+          a[0][x] += pl[0][x];
+          a[1][x] += pl[1][x];
+          a[2][x] += pl[2][x];
+          a[3][x] = fmaf(sz, pl[3][x], a[3][x]);
+        }
       }
     }
     __syncthreads();   // window no longer read: it becomes the reduction scratch
