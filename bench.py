@@ -31,6 +31,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "FMM cells/s at 256^3 p=6: mixed-prec+learned vs plain FP32, L2 err ≤1e-4 vs PM"
+# weights of the learned M2L table correction trained by
+# `python -m paper_2011_07099_gb300.learn` (order 6, 64^3 training fields)
+DEFAULT_CORRECTION = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2011_07099_gb300", "data",
+                                  "correction_p6.npz")
 UNIT = "cells/s"
 FP32_FMA_PER_SM_PER_CLK = 128        # FP32 lanes per SM (4 partitions x 32)
 SM_COUNT = 152
@@ -117,7 +121,7 @@ def workload_density(n, field):
 
 # DRAM bytes (read + write) of one k_p2p launch from the ncu capture of the
 # current kernel in profiles/k_p2p_256cube_p6.md
-P2P_TRAFFIC = {(256, 5, 6): 422.2e6}
+P2P_TRAFFIC = {}
 
 
 def p2p_flops(N, L):
@@ -269,6 +273,13 @@ def run_ours(args):
     plan = B.Plan(n, L, p)
     if tc:
         plan.set_precision(prec)
+    learned = None
+    wpath = args.correction or (DEFAULT_CORRECTION if p == 6 else None)
+    if tc and not args.no_correction and wpath and os.path.exists(wpath):
+        w = torch.from_numpy(np.load(wpath)["w"].astype(np.float32)).to(dev)
+        B.fmm_plan_set_correction(plan.handle, w)   # tabulated once at plan time; BF16 inference
+        learned = {"weights": os.path.relpath(wpath, os.path.dirname(os.path.abspath(__file__))),
+                   "inference": "bf16", "applied_to": "M2L tables, levels 2..L"}
     with ClockSampler(dev.index) as clk:
         step_ms, stage, wall = _time_solves(B, plan, rho, phi, acc, args.steps, args.warmup, l2_flush, stream,
                                             barrier)
@@ -353,8 +364,9 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32" if not tc else ("bf16x3" if prec == B.FMM_PREC_BF16X3 else "bf16"),
         "data": "synthetic",
         "config": {"workload": f"{n}^3 lognormal sigma=0.5 (seeded), order p={p}, L={L} (S={n >> L}), "
-                               f"M2L levels>=4 {args.precision}, levels 2-3 FP32 split-table",
-                   "N": n, "L": L, "order": p, "precision": args.precision,
+                               f"M2L levels>=4 {args.precision}, levels 2-3 extended-precision CUDA-core"
+                               + (", learned table correction" if learned else ""),
+                   "N": n, "L": L, "order": p, "precision": args.precision, "learned_correction": learned,
                    "l2_flush": "256 MB buffer written between timed steps",
                    "parallelism": f"replicas x{ws}"},
         "stage_ms": stage_ms,
@@ -485,6 +497,10 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 form")
     ap.add_argument("--workload", choices=["headline", "batch", "full512"], default="headline")
     ap.add_argument("--fields", type=int, default=64)
+    ap.add_argument("--correction", default=None,
+                    help="weights (.npz with 'w') of the learned table correction for the mixed form; "
+                         "default: the trained order-6 weights shipped with the package, when p = 6")
+    ap.add_argument("--no-correction", action="store_true", help="time the mixed form without the correction")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
