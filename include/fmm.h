@@ -123,6 +123,15 @@ int fmm_plan_inject_fault(fmm_plan* plan, int kind);
  * FMM_ERR_ARG outside 1..189. */
 int fmm_plan_set_m2l_group(fmm_plan* plan, int offsets_per_partial);
 
+/* Tensor-core M2L: number of CTAs (1, 2 or 4) launched as one thread-block
+ * cluster along the target tiles.  They share a row tile and a child type,
+ * hence the same translation tiles, which each copies 1/ctas of and
+ * multicasts to the others: the L2 traffic of those tiles falls by that
+ * factor.  Levels whose target-tile count is not a multiple run without
+ * clusters.  Results do not depend on it.  Default 2.  FMM_ERR_ARG
+ * otherwise. */
+int fmm_plan_set_m2l_cluster(fmm_plan* plan, int ctas);
+
 /* Mixed-precision forms: the first tree level whose M2L (eq. fmm2) runs on
  * the tensor cores; coarser levels run the FP32 CUDA-core kernel.  Default
  * and minimum 4 (levels 2 and 3 always use the extended-precision CUDA-core

@@ -336,6 +336,12 @@ int fmm_plan_inject_fault(fmm_plan* plan, int kind) {
   return set_err(FMM_OK);
 }
 
+int fmm_plan_set_m2l_cluster(fmm_plan* plan, int ctas) {
+  if (!plan || (ctas != 1 && ctas != 2 && ctas != 4)) return set_err(FMM_ERR_ARG);
+  reinterpret_cast<Plan*>(plan)->tc_cluster = ctas;
+  return set_err(FMM_OK);
+}
+
 int fmm_plan_set_m2l_group(fmm_plan* plan, int offsets_per_partial) {
   if (!plan || offsets_per_partial < 1 || offsets_per_partial > fmm::kMaxOffsets) return set_err(FMM_ERR_ARG);
   reinterpret_cast<Plan*>(plan)->tc_group = offsets_per_partial;

@@ -96,6 +96,7 @@ struct Plan {
   void* Apre[kMaxLevel + 1] = {};          // precomputed split translation tiles per offset slot
   int tc_group = 2;                        // offsets accumulated per TMEM partial before promotion
   int tc_min_level = kTcMinLevel;          // first level on the tensor cores in the mixed forms
+  int tc_cluster = 2;                      // CTAs per cluster sharing the tensor-core A tiles (1, 2, 4)
   // learned table correction (MLP weights) and its training buffers
   float* corr_w = nullptr;                 // mlp::kParams weights (device) or unset
   int has_corr = 0;

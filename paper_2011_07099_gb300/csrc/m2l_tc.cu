@@ -71,7 +71,12 @@ constexpr int kOffSlots = 343;
 
 __device__ __forceinline__ void producer_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kProd) : "memory"); }
 
-template <int P, int MODE>
+// CL > 1: the kernel runs as clusters of CL CTAs along the target-tile axis
+// (same row tile, same child type, so the same A tiles): each CTA copies 1/CL
+// of every A stage and multicasts it to the whole cluster, and every CTA's MMA
+// completion releases the stage in all of them (their empty barriers count CL
+// arrivals), which divides the A traffic from L2 by CL.
+template <int P, int MODE, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
 k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre,
          const int8_t* __restrict__ offs, int n_off, int level, int group,
@@ -98,12 +103,14 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
   const uint32_t par0 = (uint32_t)nt * kNT;
   const int8_t* my_offs = offs + (size_t)ctype * n_off * 3;
   const int n_grp = (n_off + group - 1) / group;
+  const uint32_t crank = CL > 1 ? tc::cluster_ctarank() : 0u;
+  constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
 
   if (tid == 0) {
     s_err = 0;
     for (int i = 0; i < ST; ++i) {
       tc::mbar_init(&full[i], kProd + 1);      // kProd cp.async-completion arrivals + the A expect_tx arrival
-      tc::mbar_init(&empty[i], 1);
+      tc::mbar_init(&empty[i], CL);          // one MMA completion per CTA of the cluster
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&pfull[b], 1);
@@ -114,6 +121,7 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
   if (warp == 0) tc::tmem_alloc(&tmem_holder, kTmemCols);
   tc::fence_before_sync();
   __syncthreads();
+  if (CL > 1) tc::cluster_sync();            // every CTA's barriers exist before any multicast
   tc::fence_after_sync();
   const uint32_t tmem = tmem_holder;
   const uint32_t t_tot = tmem + 256, t_cmp = tmem + 384;
@@ -156,7 +164,10 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
               tc::mma_bf16(dst, al, bh, IDESC, 1u);
             }
           }
-          tc::mma_commit(&empty[st]);
+          if (CL > 1)
+            tc::mma_commit_mc(&empty[st], kMask);
+          else
+            tc::mma_commit(&empty[st]);
         }
         if (ok && ((io % group) == group - 1 || io == n_off - 1)) tc::mma_commit(&pfull[b]);
       }
@@ -192,9 +203,16 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
         const uint32_t sA = smem_base + st * STAGE_BYTES;
         const uint32_t sB = sA + NSPLIT * kTileBytes;
         if (pt == 0) {
-          tc::mbar_arrive_expect_tx(&full[st], A_TX);
-          tc::bulk_g2s(sA, atile + (size_t)ch * 2 * kTileBytes, kTileBytes, &full[st]);
-          if (MODE == 3) tc::bulk_g2s(sA + kTileBytes, atile + ((size_t)ch * 2 + 1) * kTileBytes, kTileBytes, &full[st]);
+          tc::mbar_arrive_expect_tx(&full[st], A_TX);     // all of A lands here, 1/CL from each CTA
+          if (CL > 1) {
+            constexpr uint32_t chunk = A_TX / CL;
+            tc::bulk_g2s_mc(sA + crank * chunk, atile + (size_t)ch * 2 * kTileBytes + crank * chunk, chunk,
+                            &full[st], kMask);
+          } else {
+            tc::bulk_g2s(sA, atile + (size_t)ch * 2 * kTileBytes, kTileBytes, &full[st]);
+            if (MODE == 3)
+              tc::bulk_g2s(sA + kTileBytes, atile + ((size_t)ch * 2 + 1) * kTileBytes, kTileBytes, &full[st]);
+          }
         }
 #pragma unroll
         for (int pass = 0; pass < 8; ++pass) {
@@ -211,6 +229,14 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
     }
     tc::cp_async_wait<0>();
     asm volatile("cp.async.wait_all;" ::: "memory");
+    // cluster tail: the last MMA completions of every CTA arrive on this
+    // CTA's empty barriers; wait for them (bounded) so that nothing is still
+    // to arrive here when the cluster leaves
+    if (CL > 1 && ok && pt == 0) {
+      const int total = n_off * NCH;
+      for (int it = total - ST > 0 ? total - ST : 0; it < total && ok; ++it)
+        if (!tc::mbar_wait_bounded(&empty[it % ST], (uint32_t)(it / ST) & 1u, kWaitNs)) ok = false;
+    }
     if (!ok) atomicExch(&s_err, 1);
   } else {
     // ------------------------------------------------------------ drain warps
@@ -277,6 +303,7 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
   }
   tc::fence_before_sync();
   __syncthreads();
+  if (CL > 1) tc::cluster_sync();            // no CTA leaves while a peer may still signal it
   if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
   if (tid == 0 && s_err) atomicExch(err, 1);
 }
@@ -335,7 +362,13 @@ constexpr size_t smem_bytes() {
 
 template <int P, int MODE>
 cudaError_t setup_one() {
-  return cudaFuncSetAttribute(k_m2l_tc<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<P, MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes<P, MODE>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_m2l_tc<P, MODE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem_bytes<P, MODE>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_m2l_tc<P, MODE, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem_bytes<P, MODE>());
 }
 
@@ -343,9 +376,34 @@ template <int P, int MODE>
 cudaError_t launch_one(Plan& Pl, int level, cudaStream_t s) {
   const uint32_t n_par = 1u << (3 * (level - 1));
   dim3 grid(TcShape<P, MODE>::MT, (n_par + kNT - 1) / kNT, 8);
-  k_m2l_tc<P, MODE><<<grid, kThreads, smem_bytes<P, MODE>(), s>>>(
-      static_cast<const __nv_bfloat16*>(Pl.Mbf_hi[level]), static_cast<const uint8_t*>(Pl.Apre[level]),
-      Pl.offsets[level], Pl.n_off[level], level, Pl.tc_group, Pl.F[level], Pl.d_err, Pl.wait_ns, Pl.inject_stall);
+  const __nv_bfloat16* Msp = static_cast<const __nv_bfloat16*>(Pl.Mbf_hi[level]);
+  const uint8_t* Apre = static_cast<const uint8_t*>(Pl.Apre[level]);
+  const int cl = Pl.tc_cluster;
+  if (cl > 1 && grid.y % cl == 0) {
+    // clusters of CTAs along the target tiles share (multicast) their A tiles
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem_bytes<P, MODE>();
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = cl;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cl == 4)
+      return cudaLaunchKernelEx(&cfg, k_m2l_tc<P, MODE, 4>, Msp, Apre, (const int8_t*)Pl.offsets[level],
+                                Pl.n_off[level], level, Pl.tc_group, Pl.F[level], Pl.d_err, Pl.wait_ns,
+                                Pl.inject_stall);
+    return cudaLaunchKernelEx(&cfg, k_m2l_tc<P, MODE, 2>, Msp, Apre, (const int8_t*)Pl.offsets[level],
+                              Pl.n_off[level], level, Pl.tc_group, Pl.F[level], Pl.d_err, Pl.wait_ns,
+                              Pl.inject_stall);
+  }
+  k_m2l_tc<P, MODE, 1><<<grid, kThreads, smem_bytes<P, MODE>(), s>>>(
+      Msp, Apre, Pl.offsets[level], Pl.n_off[level], level, Pl.tc_group, Pl.F[level], Pl.d_err, Pl.wait_ns,
+      Pl.inject_stall);
   return cudaGetLastError();
 }
 

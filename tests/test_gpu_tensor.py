@@ -73,6 +73,28 @@ def test_bf16x3_promotion_group_sizes(B, group):
     assert _rel(acc, og) <= tol
 
 
+@pytest.mark.parametrize("ctas", [1, 2, 4])
+def test_cluster_multicast_gives_identical_results(B, ctas):
+    # clusters only change where the translation tiles come from: results are
+    # bitwise the same for every cluster size
+    N, L, p = 64, 4, 4
+    rho = inputs.plummer(N, n_clumps=16, seed=6)
+    d = torch.from_numpy(rho).cuda()
+    outs = []
+    for c in (1, ctas):
+        plan = B.Plan(N, L, p)
+        plan.set_precision(B.FMM_PREC_BF16X3)
+        B.fmm_plan_set_m2l_cluster(plan.handle, c)
+        phi, acc = plan.solve(d)
+        torch.cuda.synchronize()
+        assert B.lib().fmm_plan_check(plan.handle) == B.FMM_OK
+        outs.append((phi.clone(), acc.clone()))
+        plan.close()
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    ophi, og = ofmm.solve(rho, L, p)
+    assert _rel(outs[1][0].cpu().numpy(), ophi) <= TOL_BF16X3
+
+
 def test_bf16_matches_oracle(B):
     N, L, p = 64, 4, 4
     rho = inputs.lognormal(N, sigma=0.5, seed=1)
