@@ -121,7 +121,7 @@ def workload_density(n, field):
 
 # DRAM bytes (read + write) of one k_p2p launch from the ncu capture of the
 # current kernel in profiles/k_p2p_256cube_p6.md
-P2P_TRAFFIC = {}
+P2P_TRAFFIC = {(256, 5, 6): 419.8e6}
 
 
 def p2p_flops(N, L):

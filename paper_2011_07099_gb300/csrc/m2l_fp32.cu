@@ -425,9 +425,23 @@ int m2l_fp32_splits(const Plan& P, int level) {
   if (level > kExtTopLevel) return 1;     // fine levels have targets enough
   const int nt = P.p * P.p * P.p > 256 ? 4 : 8;
   const long ctas = (long)(((1u << (3 * (level - 1))) + nt - 1) / nt) * 8;
-  long want = (2L * P.num_sms + ctas - 1) / ctas;
-  if (want > P.n_off[level]) want = P.n_off[level];
-  return want < 1 ? 1 : (int)want;
+  const long sms = P.num_sms > 0 ? P.num_sms : 1;
+  // at least ~4 waves of one CTA per SM, and the range count whose last wave
+  // is fullest (these CTAs hold one SM each: registers)
+  long lo = (4 * sms + ctas - 1) / ctas, hi = 3 * lo;
+  if (hi > P.n_off[level]) hi = P.n_off[level];
+  if (lo > hi) lo = hi;
+  long best = lo < 1 ? 1 : lo;
+  double best_eff = -1.0;
+  for (long ns = best; ns <= hi; ++ns) {
+    const long waves = (ctas * ns + sms - 1) / sms;
+    const double eff = (double)(ctas * ns) / (double)(waves * sms);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = ns;
+    }
+  }
+  return (int)best;
 }
 
 cudaError_t setup_m2l_fp32(const Plan& P) {
