@@ -112,6 +112,24 @@ def _dist():
     return ws, rank, local
 
 
+def slowest_rank_ms(ms, ws, device=None):
+    """The step time of the whole job: the maximum over the ranks (one
+    independent field per rank, no data-path collective; this all-reduce
+    only aggregates the timing)."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_cells_per_s(ws, n, ms):
+    """Cells of all ranks over the slowest rank's step time (weak scaling)."""
+    return ws * n ** 3 / (ms / 1000.0)
+
+
 def workload_density(n, field):
     from paper_2011_07099_gb300 import inputs
     # the headline workload: 1 + 0.5 lognormal(sigma = 0.5), k^-2 Gaussian field,
@@ -283,13 +301,8 @@ def run_ours(args):
     with ClockSampler(dev.index) as clk:
         step_ms, stage, wall = _time_solves(B, plan, rho, phi, acc, args.steps, args.warmup, l2_flush, stream,
                                             barrier)
-    ms = statistics.mean(step_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * n ** 3 / (ms / 1000.0)
+    ms = slowest_rank_ms(statistics.mean(step_ms), ws, dev)
+    value = whole_job_cells_per_s(ws, n, ms)
     result_phi = phi.cpu().numpy() if (rank == 0 and ws == 1 and not args.no_cpu_baseline) else None
     result_acc = acc.cpu().numpy() if result_phi is not None else None
 
@@ -307,13 +320,8 @@ def run_ours(args):
         pplan = B.Plan(n, L, p)
         pms, pstage, _ = _time_solves(B, pplan, rho, phi, acc, max(1, min(args.steps, 3)), max(1, min(args.warmup, 2)),
                                       l2_flush, stream, barrier)
-        pm_ = statistics.mean(pms)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([pm_], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            pm_ = float(t.item())
-        plain = {"value": ws * n ** 3 / (pm_ / 1000.0), "ms_per_step": pm_,
+        pm_ = slowest_rank_ms(statistics.mean(pms), ws, dev)
+        plain = {"value": whole_job_cells_per_s(ws, n, pm_), "ms_per_step": pm_,
                  "m2l_ms": statistics.mean(s[B.FMM_TIME_M2L] for s in pstage),
                  "p2p_ms": statistics.mean(s[B.FMM_TIME_P2P] for s in pstage)}
         pplan.close()
