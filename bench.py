@@ -250,11 +250,40 @@ def _time_solves(B, plan, rho, phi, acc, steps, warmup, l2_flush, stream, barrie
     return step_ms, stage, wall
 
 
-def launches_per_solve(L, tc):
-    # mean (2) + P2M + M2M per level + M2L per level (+ split kernel on tensor
-    # levels) + L2L per level + P2P
-    m2l = sum(2 if (tc and lev >= 4) else 1 for lev in range(2, L + 1))
+def launches_per_solve(L, tc, p=6):
+    # mean (2) + P2M + M2M per level + M2L per level + L2L per level + P2P;
+    # M2L of the coarse levels (2-3, and every level above the leaves at
+    # order >= 7) adds the FP64 range-sum kernel, tensor-core levels the
+    # BF16 split kernel
+    wide = lambda lev: lev <= 3 or (p >= 7 and lev < L)
+    tc_first = max(4, L) if p >= 7 else 4
+    m2l = sum(2 if (wide(lev) or (tc and lev >= tc_first)) else 1 for lev in range(2, L + 1))
     return 2 + 1 + (L - 2) + m2l + (L - 2) + 1
+
+
+def solve_roofline(n, L, p, tc, ms, peaks):
+    """Ideal time of the whole solve (each step at its own bound: FP32 FMA,
+    BF16 tensor (executed products), HBM bytes) against the measured step."""
+    fp32 = 152 * 128 * 2 * 2.07e9
+    bf16 = peaks.get("bf16_tflops_sustained", 1700.0) * 1e12
+    hbm = peaks.get("hbm_gbs", 6500.0) * 1e9
+    p3 = p ** 3
+    tc_first = max(4, L) if p >= 7 else 4
+    t = {"p2p": p2p_flops(n, L) / fp32, "m2l_cuda_cores": 0.0, "m2l_tensor": 0.0}
+    for lev in range(2, L + 1):
+        f = 2.0 * 4 * p3 * p3 * (37 if lev == 2 else 189) * 8 ** lev
+        if tc and lev >= tc_first:
+            t["m2l_tensor"] += 3 * f / bf16
+        else:
+            t["m2l_cuda_cores"] += f / fp32
+    bytes_ = 4 * n ** 3 * 2 + 4 * p3 * 8 ** L                              # mean + P2M
+    bytes_ += sum(9 * 4 * p3 * 8 ** lev for lev in range(2, L))          # M2M
+    bytes_ += sum(4 * 4 * p3 * 8 ** lev * 17 for lev in range(2, L))     # L2L (parent + children read/write)
+    t["hbm_passes"] = bytes_ / hbm
+    ideal = sum(t.values()) * 1e3
+    return {"ideal_ms": ideal, "measured_ms": ms, "frac": ideal / ms,
+            "terms_ms": {k: v * 1e3 for k, v in t.items()},
+            "peaks": "FP32 80.5 TFLOP/s (derived), BF16 sustained and HBM from MEASURED_PEAKS.json"}
 
 
 def run_ours(args):
@@ -384,7 +413,8 @@ def run_ours(args):
         "roofline_m2l": roof_m2l,
         "e2e": {"value": ws * n ** 3 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * n ** 3,
                 "d2h_bytes_per_step": 16 * n ** 3},
-        "gpu_launches": launches_per_solve(L, tc) * args.steps,
+        "gpu_launches": launches_per_solve(L, tc, p) * args.steps,
+        "solve_roofline": solve_roofline(n, L, p, tc, ms, peaks),
         "clocks": clocks,
     }
     if plain is not None:
