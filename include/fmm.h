@@ -48,9 +48,11 @@ typedef struct fmm_plan fmm_plan;
 #define FMM_ERR_UNSUPPORTED 6   /* valid request this build does not implement */
 
 /* ---- M2L precision modes (fmm_plan_set_precision) -------------------- */
-#define FMM_PREC_FP32    0  /* plain form: every stage FP32 on CUDA cores      */
-#define FMM_PREC_BF16    1  /* M2L levels >= 4 on tcgen05 tensor cores, BF16
-                               operands, FP32 accumulation in TMEM            */
+#define FMM_PREC_FP32    0  /* plain form: CUDA cores, FP32 with the extended-
+                               precision coarse levels described below        */
+#define FMM_PREC_BF16    1  /* M2L levels >= 4 (order >= 7: the leaf level) on
+                               tcgen05 tensor cores, BF16 operands, FP32
+                               accumulation in TMEM                           */
 #define FMM_PREC_BF16X3  2  /* as BF16 with split products hi*hi+hi*lo+lo*hi */
 
 /* ---- plan lifecycle -------------------------------------------------- */
@@ -97,11 +99,15 @@ int fmm_solve_host(fmm_plan* plan, const float* density_host,
 /* ---- configuration ------------------------------------------------------ */
 
 /* Select the M2L arithmetic (FMM_PREC_*).  Takes effect at the next solve.
- * FMM_PREC_BF16 / FMM_PREC_BF16X3 apply to levels >= 4; levels 2 and 3 keep
- * the FP32 split-table contraction (their long-range sums cancel most).  The
- * first tensor-core selection allocates and tabulates the split BF16 tables
- * and multipole buffers (synchronous).  Order 1 ignores the tensor-core modes.
- * FMM_ERR_ARG for an unknown mode. */
+ * FMM_PREC_BF16 / FMM_PREC_BF16X3 apply to levels >= 4 (see
+ * fmm_plan_set_tc_min_level; at order >= 7 only the leaf level).  In every
+ * mode the coarse levels, whose long-range sums cancel most, run on the CUDA
+ * cores in extended precision: level 2 in double-float (error-free products
+ * and sums), level 3 with split tables, both reduced in FP64 into FP64 local
+ * fields; at order >= 7 every level above the leaves does the same.  The
+ * first tensor-core selection allocates and tabulates the split BF16 tables,
+ * translation tiles and multipole buffers (synchronous).  Order 1 ignores
+ * the tensor-core modes.  FMM_ERR_ARG for an unknown mode. */
 int fmm_plan_set_precision(fmm_plan* plan, int mode);
 
 /* Limit of every bounded device-side wait (pipeline barriers of the
