@@ -1,7 +1,8 @@
 // Inline-PTX helpers for the 5th-generation tensor cores (tcgen05) of sm_103a:
 // TMEM allocation, shared-memory matrix descriptors, the instruction
-// descriptor of kind::f16, MMA issue/commit, bounded mbarrier waits and TMEM
-// loads.  Written from the public PTX ISA description of tcgen05.
+// descriptor of kind::f16, MMA issue/commit (also multicast to a cluster),
+// bounded mbarrier waits, TMEM loads/stores, bulk and cp.async copies and
+// cluster barriers.  Written from the public PTX ISA descriptions.
 #pragma once
 
 #include <cstdint>
@@ -108,49 +109,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t phase
   }
 }
 
-// -------------------------------------------------------------- TMEM loads
-// 32 lanes x 32 bits, 16 consecutive columns: thread i of the warp gets row
-// (lane base + i), columns [col, col + 16).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 32 lanes x 32 bits, 16 consecutive columns, store direction.
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float v[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-          taddr),
-      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
-      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
-      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
-      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
-      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
-      : "memory");
-}
+// ------------------------------------------------------- TMEM loads, stores
+// Wait until this thread's tcgen05.st / tcgen05.ld have completed.
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-// Load without the trailing wait (several loads may be in flight); the caller
-// issues tmem_wait_ld() before using the registers.
-__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t r[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// 32 lanes x 32 bits, 32 consecutive columns (no trailing wait).
+// 32 lanes x 32 bits, 32 consecutive columns: thread i of the warp gets row
+// (lane base + i).  No trailing wait: several loads may be in flight, and the
+// caller issues tmem_wait_ld() before using the registers.
 __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t r[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
