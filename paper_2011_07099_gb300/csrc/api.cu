@@ -117,8 +117,6 @@ void free_plan(Plan* P) {
   }
   cudaFree(P->w_p2m);
   cudaFree(P->w_m2m);
-  cudaFree(P->wd_p2m);
-  cudaFree(P->wd_m2m);
   cudaFree(P->stage_in);
   cudaFree(P->stage_out);
   for (auto& e : P->ev)
@@ -200,15 +198,14 @@ fmm_plan* fmm_plan_create(int N, int L, int order) {
     if (ok && p >= fmm::kWideOrder) ok = dev_alloc(&P->M64[l], nodes * p3);
   }
   ok = ok && dev_alloc(&P->near_tab, (size_t)8 * S * S * S) && dev_alloc(&P->w_p2m, (size_t)p * S) &&
-       dev_alloc(&P->w_m2m, (size_t)p * 2 * p) && dev_alloc(&P->wd_p2m, (size_t)p * S) &&
-       dev_alloc(&P->wd_m2m, (size_t)p * 2 * p);
+       dev_alloc(&P->w_m2m, (size_t)p * 2 * p);
   if (!ok) {
     free_plan(P);
     set_err(FMM_ERR_ALLOC);
     return nullptr;
   }
   // host-side constants: Lagrange weights and interaction lists
-  // FP64 weights for the upward pass, (hi, lo) FP32 pairs for the downward pass
+  // Lagrange weights in FP64 on the host, stored as (hi, lo) FP32 pairs
   std::vector<double> wp = lagrange_weights(p, S), wm = lagrange_weights(p, 2 * p);
   auto split = [](const std::vector<double>& v) {
     std::vector<float2> o(v.size());
@@ -220,9 +217,7 @@ fmm_plan* fmm_plan_create(int N, int L, int order) {
   };
   std::vector<float2> wp2 = split(wp), wm2 = split(wm);
   bool cok = cudaMemcpy(P->w_p2m, wp2.data(), wp2.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(P->w_m2m, wm2.data(), wm2.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(P->wd_p2m, wp.data(), wp.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(P->wd_m2m, wm.data(), wm.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+             cudaMemcpy(P->w_m2m, wm2.data(), wm2.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess;
   for (int l = 2; l <= L && cok; ++l) {
     std::vector<int8_t> all;
     int count = -1;

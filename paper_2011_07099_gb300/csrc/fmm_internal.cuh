@@ -82,12 +82,10 @@ struct Plan {
   // FP64 as well (M2M writes both copies; M2L reads them as hi + lo).
   double* M64[kMaxLevel + 1] = {};
   float4* tab[kMaxLevel + 1] = {};  // (G, -dG/dx, -dG/dy, -dG/dz) at n dx_l, n in [-(4p-1), 4p-1]^3
-  float4* tab_lo[kMaxLevel + 1] = {};  // v - fl32(v) of the same entries, 4 fields (levels 2..kExtTopLevel)
+  float4* tab_lo[kMaxLevel + 1] = {};  // v - fl32(v) of the same entries, 4 fields (wide levels)
   float4* near_tab = nullptr;       // the same at cell spacing for |d_i| in [0, 2S-1], folded
   float2* w_p2m = nullptr;          // Lagrange weights [p][S] as (hi, lo): gridlet s at cell c
   float2* w_m2m = nullptr;          // Lagrange weights [p][2p] as (hi, lo): parent s at child point u
-  double* wd_p2m = nullptr;         // the same weights in FP64 for the upward pass
-  double* wd_m2m = nullptr;
   int8_t* offsets[kMaxLevel + 1] = {};  // per level: [8 child types][n_off][3] (dx, dy, dz) = T - S
   // tensor-core M2L (levels >= kTcMinLevel, allocated on the first mixed-precision solve)
   uint4* tab_bf[kMaxLevel + 1] = {};       // per table entry, per field: bf16 hi | bf16 lo << 16
@@ -193,32 +191,59 @@ __device__ inline void contract_mid(const float* __restrict__ in, float* __restr
   }
 }
 
-// FP64 variant for the upward pass: the cell masses of a mean-free field and
-// the partial sums of P2M/M2M cancel, and every node of a near-uniform region
-// rounds the same way in FP32, so those errors add up coherently across the
-// mesh instead of averaging out.
-__device__ inline void contract_mid_d(const double* __restrict__ in, double* __restrict__ out, int A, int Kin,
-                                      int Kout, int B, const double* __restrict__ W, int ldw, int tid, int nthr,
-                                      bool wt = false) {
+// ---------------------------------------------------------- double-float
+// Values as unevaluated sums hi + lo of two FP32 numbers (~48 significant
+// bits) computed with error-free transformations (TwoProd by FMA, TwoSum;
+// Ogita, Rump and Oishi, "Accurate sum and dot product", 2005).  The _rn
+// intrinsics keep the compiler from contracting the transformations into
+// FMAs.  On this part the FP64 pipe runs at 1/64 of the FP32 rate, so the
+// upward pass and the coarse L2L run ~10x faster this way than in FP64.
+__device__ __forceinline__ float2 df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z)));
+}
+__device__ __forceinline__ float2 df_from_double(double d) {
+  const float h = (float)d;
+  return make_float2(h, (float)(d - (double)h));
+}
+__device__ __forceinline__ double df_to_double(float2 v) { return (double)v.x + (double)v.y; }
+
+// contract_mid in double-float: inputs, weights and outputs are (hi, lo)
+// pairs; each output is normalised (hi = the FP32 rounding of the sum).
+__device__ inline void contract_mid_df(const float2* __restrict__ in, float2* __restrict__ out, int A, int Kin,
+                                       int Kout, int B, const float2* __restrict__ W, int ldw, bool wt, int tid,
+                                       int nthr) {
   const int total = A * Kout * B;
   for (int i = tid; i < total; i += nthr) {
     const int b = i % B;
     const int s = (i / B) % Kout;
     const int a = i / (B * Kout);
-    const double* src = in + (size_t)a * Kin * B + b;
-    double acc = 0.0;
-    for (int k = 0; k < Kin; ++k) acc = fma(wt ? W[k * ldw + s] : W[s * ldw + k], src[k * B], acc);
-    out[i] = acc;
+    const float2* src = in + (size_t)a * Kin * B + b;
+    float hs = 0.f, lc = 0.f;
+    for (int k = 0; k < Kin; ++k) {
+      const float2 w = wt ? W[k * ldw + s] : W[s * ldw + k];
+      const float2 x = src[k * B];
+      const float pr = __fmul_rn(w.x, x.x);
+      const float pe = fmaf(w.x, x.x, -pr);            // exact product error
+      const float2 t = df_two_sum(hs, pr);
+      hs = t.x;
+      lc = fmaf(w.x, x.y, fmaf(w.y, x.x, __fadd_rn(lc, __fadd_rn(pe, t.y))));
+    }
+    const float sum = __fadd_rn(hs, lc);
+    out[i] = make_float2(sum, __fsub_rn(lc, __fsub_rn(sum, hs)));
   }
 }
 
-__device__ inline void contract3_d(const double* in, double* t1, double* t2, double* out, int Kin, int Kout,
-                                   const double* W, int ldw, int tid, int nthr, bool wt = false) {
-  contract_mid_d(in, t1, Kin * Kin, Kin, Kout, 1, W, ldw, tid, nthr, wt);
+// 3-D separable contraction [Kin]^3 -> [Kout]^3 of one field in double-float
+// (scratch t1: Kin*Kin*Kout, t2: Kin*Kout*Kout pairs).  Ends with __syncthreads().
+__device__ inline void contract3_df(const float2* in, float2* t1, float2* t2, float2* out, int Kin, int Kout,
+                                    const float2* W, int ldw, bool wt, int tid, int nthr) {
+  contract_mid_df(in, t1, Kin * Kin, Kin, Kout, 1, W, ldw, wt, tid, nthr);
   __syncthreads();
-  contract_mid_d(t1, t2, Kin, Kin, Kout, Kout, W, ldw, tid, nthr, wt);
+  contract_mid_df(t1, t2, Kin, Kin, Kout, Kout, W, ldw, wt, tid, nthr);
   __syncthreads();
-  contract_mid_d(t2, out, 1, Kin, Kout, Kout * Kout, W, ldw, tid, nthr, wt);
+  contract_mid_df(t2, out, 1, Kin, Kout, Kout * Kout, W, ldw, wt, tid, nthr);
   __syncthreads();
 }
 
