@@ -231,8 +231,10 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
 // error-free transformations (TwoProd by FMA, TwoSum; Ogita, Rump and Oishi,
 // "Accurate sum and dot product", 2005), about 48 significant bits in FP32
 // instructions; the FP64 pipe of this part would be ~6x slower.
+// At high order (512 threads) one CTA per SM is the shared-memory limit
+// anyway; saying so lets each thread keep its 2 x 4 x NT sums in registers.
 template <int P>
-__global__ void __launch_bounds__(M2LShape<P>::THREADS)
+__global__ void __launch_bounds__(M2LShape<P>::THREADS, P >= kWideOrder ? 1 : 2)
 k_m2l_df(const float* __restrict__ M, float* __restrict__ F, const float4* __restrict__ tab,
          const float4* __restrict__ tab_lo, const int8_t* __restrict__ offs, int n_off, int level, int per_split,
          size_t split_stride, int pairs, const double* __restrict__ M64) {
