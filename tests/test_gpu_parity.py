@@ -181,3 +181,30 @@ def test_full_size_sampled_leaves_match_oracle(B, N, L, p, cfg, leaves):
     assert _rel(got[:, 0], ref[:, 0]) <= TOL_FP32
     assert _rel(got[:, 1:], ref[:, 1:]) <= TOL_FP32
     plan.close()
+
+
+def test_full_scale_512_order8_sampled_leaves(B):
+    # the full-scale workload exactly as bench.py --workload full512 runs it
+    # (512^3, p = 8, L = 6, clustered recipe on the device), plain and mixed
+    # forms against the oracle at two sampled leaves (one oracle evaluation)
+    N, L, p = 512, 6, 8
+    leaves = np.array([[1, 2, 3], [40, 0, 63]])
+    rho_t = inputs.config_density_torch(4, torch.device("cuda", 0), n=N)
+    rho = rho_t.cpu().numpy()
+    ref = ofmm.solve_at(rho, L, p, leaves)
+    S = N >> L
+    for prec, tol in ((0, TOL_FP32), (B.FMM_PREC_BF16X3, 2e-5)):
+        plan = B.Plan(N, L, p)
+        if prec:
+            plan.set_precision(prec)
+        phi, acc = plan.solve(rho_t)
+        torch.cuda.synchronize()
+        got = np.stack([torch.cat([phi[a * S:(a + 1) * S, b * S:(b + 1) * S, c * S:(c + 1) * S].reshape(1, -1),
+                                   acc[:, a * S:(a + 1) * S, b * S:(b + 1) * S, c * S:(c + 1) * S].reshape(3, -1)]
+                                  ).cpu().numpy()
+                        for a, b, c in leaves])
+        plan.close()
+        del phi, acc
+        e_phi, e_g = _rel(got[:, 0], ref[:, 0]), _rel(got[:, 1:], ref[:, 1:])
+        print(f"512^3 p=8 precision {prec}: phi {e_phi:.3e} g {e_g:.3e}")
+        assert e_phi <= tol and e_g <= tol
