@@ -1,0 +1,237 @@
+"""Non-periodic references and the Green's-function error of eq. gerr, FP64
+(test infrastructure: the reference side of the paper's accuracy experiment,
+Sec. 3; no GPU counterpart yet).
+
+The experiment of Sec. 3 separates the two errors of a periodic FMM solution
+against a PM solution: the error of the multipole expansion, measured on the
+same problem without periodic boundaries, and the error of the Green's
+function, what is left (eq. gerr):
+
+    Delta g = | g_FMM^P - g_PM^P - (g_FMM^NP - g_PM^NP) |,
+
+with absolute norms L_MAX (maximum over cells) and L2 (root mean square over
+cells) for a unit mass in a unit box (Sec. 3: the characteristic acceleration
+is 1, so the absolute error is a relative one).  PM accelerations come from
+the potential by the 4th-order central difference (Sec. 3), FMM accelerations
+from the expansion.
+
+Readings (the paper is brief here):
+  * the non-periodic problem has the isolated Green's function G_0 =
+    -1/(4 pi r) everywhere, no mean removal (masses m = rho / N^3), and the
+    same cell self term G(0) as the periodic solver;
+  * the non-periodic PM is the zero-padded (Hockney) FFT convolution, padded
+    to (2N + 4)^3 so that its potential two cells outside the box (from the
+    same convolution) feeds the finite difference at the box faces;
+  * the non-periodic FMM keeps the tree, gridlets and operators of the
+    periodic one and drops the wrap: a node's near zone is its in-box
+    neighbours, its interaction zone the children of its parent's in-box
+    neighbours that are not its neighbours (Sec. 2, Fig. fmm without the
+    periodic translation), with G_0 in M2L and P2P;
+  * the periodic PM of eq. gerr is the spectral PM with G_K (Sec. 1 eq. gfk),
+    the PM whose agreement defines the optimal G_*.
+Open before Table 1 can be compared: the paper's FMM-HPM computes the near
+zone with the PM's own Green's function on the sub-grid (Sec. 3: it must
+match PM), and its near-zone accelerations presumably by the same finite
+difference; with an exact-gradient near zone the source-cell neighbourhood
+dominates eq. gerr (O(1) in a 16^3 corner-source test).  This module
+provides the pinned pieces: isolated PM and FMM, the 4th-order difference and
+the norms of eq. gerr.
+"""
+from functools import lru_cache
+
+import numpy as np
+
+from . import green
+from . import pm as ppm
+from .fmm import (FIELDS, all_nodes, gridlet_offsets, l2l, l2p_matrix, leaves_of, mesh_of, tensor_points,
+                  upward)
+
+FOUR_PI = 4.0 * np.pi
+
+
+def masses_isolated(rho):
+    """Mesh masses of an isolated distribution, m = rho / N^3 (no mean removal)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    return rho / float(rho.shape[0]) ** 3
+
+
+def g0_at(d, self_value):
+    """G_0 at displacements d (box units, (..., 3)); `self_value` where d = 0."""
+    r = np.sqrt(np.sum(np.asarray(d, dtype=np.float64) ** 2, axis=-1))
+    zero = r == 0.0
+    out = -1.0 / (FOUR_PI * np.where(zero, 1.0, r))
+    return np.where(zero, self_value, out)
+
+
+def grad_g0(d):
+    """grad G_0 = x / (4 pi r^3); 0 at d = 0 (the cell self force vanishes)."""
+    d = np.asarray(d, dtype=np.float64)
+    r2 = np.sum(d * d, axis=-1)
+    zero = r2 == 0.0
+    r3 = np.where(zero, 1.0, r2 * np.sqrt(r2))
+    out = d / (FOUR_PI * r3[..., None])
+    out[zero] = 0.0
+    return out
+
+
+def direct_isolated(m, self_value):
+    """Brute-force isolated sum over every pair of cells: (phi, g), g = -grad Phi.
+    O(N^6): meant for N <= 16."""
+    m = np.asarray(m, dtype=np.float64)
+    n = m.shape[0]
+    pos = ppm.offsets_grid(n).reshape(-1, 3)
+    d = (pos[:, None, :] - pos[None, :, :]) / n
+    mf = m.reshape(-1)
+    phi = g0_at(d, self_value) @ mf
+    g = -np.einsum("ijc,j->ic", grad_g0(d), mf)
+    return phi.reshape(n, n, n), np.moveaxis(g, -1, 0).reshape(3, n, n, n)
+
+
+def pm_isolated(m, self_value):
+    """Zero-padded FFT convolution of the masses with G_0 sampled at the mesh
+    offsets d/N (the Hockney method).  The padded mesh has 2N + 4 cells per
+    side, so the convolution is also exact two cells beyond every box face
+    (targets t in [-2, N + 1], offsets t - j within the kernel's
+    [-(N + 2), N + 1]), where the 4th-order difference reads it.  Returns
+    (phi on the box, phi on the padded mesh [z][y][x], box at [0, N)^3,
+    t = -1, -2 at the last two indices)."""
+    m = np.asarray(m, dtype=np.float64)
+    n = m.shape[0]
+    n2 = 2 * n + 4
+    k = np.arange(n2)
+    k = np.where(k < n2 // 2, k, k - n2).astype(np.float64)       # signed offsets in FFT order
+    dz, dy, dx = np.meshgrid(k, k, k, indexing="ij")
+    kern = g0_at(np.stack([dx, dy, dz], axis=-1) / n, self_value)
+    mp = np.zeros((n2, n2, n2))
+    mp[:n, :n, :n] = m
+    phi_pad = np.fft.irfftn(np.fft.rfftn(mp) * np.fft.rfftn(kern), s=(n2, n2, n2), axes=(0, 1, 2))
+    return phi_pad[:n, :n, :n], phi_pad
+
+
+def fd4(phi, h, axis):
+    """Central 4th-order difference d phi / dx along `axis` (periodic roll):
+    [8 (f(+1) - f(-1)) - (f(+2) - f(-2))] / (12 h) (Sec. 3)."""
+    p1, m1 = np.roll(phi, -1, axis), np.roll(phi, 1, axis)
+    p2, m2 = np.roll(phi, -2, axis), np.roll(phi, 2, axis)
+    return (8.0 * (p1 - m1) - (p2 - m2)) / (12.0 * h)
+
+
+def fd4_accel_periodic(phi):
+    """g = -grad Phi on a periodic N^3 mesh (box units), components (x, y, z)."""
+    n = phi.shape[0]
+    h = 1.0 / n
+    return -np.stack([fd4(phi, h, 2), fd4(phi, h, 1), fd4(phi, h, 0)])
+
+
+def fd4_accel_isolated(phi_pad, n):
+    """g = -grad Phi on the box from `pm_isolated`'s padded potential: the
+    stencil reaches two cells outside the box, where the padded convolution
+    holds the potential of the same masses."""
+    h = 1.0 / n
+    g = -np.stack([fd4(phi_pad, h, 2), fd4(phi_pad, h, 1), fd4(phi_pad, h, 0)])
+    return g[:, :n, :n, :n]
+
+
+# --------------------------------------------------------- isolated FMM
+def neighbours_np(level, node):
+    """The node and its in-box neighbours (no wrap)."""
+    n = 2 ** level
+    out = set()
+    for a in (-1, 0, 1):
+        for b in (-1, 0, 1):
+            for c in (-1, 0, 1):
+                q = (node[0] + a, node[1] + b, node[2] + c)
+                if all(0 <= v < n for v in q):
+                    out.add(q)
+    return out
+
+
+def interaction_list_np(level, node):
+    """Children of the parent's in-box neighbours that are not neighbours of
+    the node (Sec. 2, Fig. fmm, without the periodic wrap)."""
+    parent = tuple(i // 2 for i in node)
+    kids = set()
+    for q in neighbours_np(level - 1, parent):
+        for a in range(2):
+            for b in range(2):
+                for c in range(2):
+                    kids.add((2 * q[0] + a, 2 * q[1] + b, 2 * q[2] + c))
+    return kids - neighbours_np(level, node)
+
+
+@lru_cache(maxsize=None)
+def _m2l_kernel_g0(level, p, off_zyx):
+    """(4, p^3, p^3) matrices of eq. fmm2 with G_0 for a node offset T - S."""
+    H = 2.0 ** (-level)
+    pts = tensor_points(gridlet_offsets(p))
+    d = (np.array(off_zyx[::-1], dtype=np.float64)[None, None, :] + pts[:, None, :] - pts[None, :, :]) * H
+    G = g0_at(d, 0.0)
+    dG = grad_g0(d)
+    return np.concatenate([G[None], -np.moveaxis(dG, -1, 0)], axis=0)
+
+
+@lru_cache(maxsize=None)
+def _p2p_kernel_g0(N, S, off_zyx):
+    """Near-zone matrices (4, S^3, S^3) with G_0 between a target leaf and the
+    source leaf at offset T - S; the coincident cell uses the self term."""
+    cells = tensor_points(np.arange(S, dtype=np.float64))
+    d = (np.array(off_zyx[::-1], dtype=np.float64)[None, None, :] * S + cells[:, None, :] - cells[None, :, :]) / N
+    G = g0_at(d, green.self_term(N))
+    dG = grad_g0(d)
+    return np.concatenate([G[None], -np.moveaxis(dG, -1, 0)], axis=0)
+
+
+def solve_isolated(rho, L, p):
+    """The FMM of `fmm.solve` without periodic boundaries (see the module
+    readings).  Returns (phi (N,N,N), g (3,N,N,N))."""
+    rho = np.asarray(rho, dtype=np.float64)
+    N = rho.shape[0]
+    n = 2 ** L
+    S = N // n
+    if N % n or L < 2 or S < 1:
+        raise ValueError("need N divisible by 2^L and L >= 2")
+    m = masses_isolated(rho)
+    M = upward(m, L, p)
+    P3 = p ** 3
+    loc = None
+    for lev in range(2, L + 1):
+        nl = 2 ** lev
+        F = np.zeros((nl, nl, nl, FIELDS, P3))
+        for T in map(tuple, all_nodes(lev)):
+            for src in interaction_list_np(lev, T):
+                off = tuple(int(a - b) for a, b in zip(T, src))
+                K = _m2l_kernel_g0(lev, p, off).reshape(FIELDS * P3, P3)
+                F[T] += (K @ M[lev][src]).reshape(FIELDS, P3)
+        if loc is not None:
+            for cz in range(2):
+                for cy in range(2):
+                    for cx in range(2):
+                        F[cz::2, cy::2, cx::2] += l2l(loc, p, (cx, cy, cz))
+        loc = F
+    far = loc @ l2p_matrix(S, p).T                                 # (n,n,n,4,S^3)
+    ml = leaves_of(m, L)
+    near = np.zeros((n, n, n, FIELDS, S ** 3))
+    for T in map(tuple, all_nodes(L)):
+        for src in neighbours_np(L, T):
+            off = tuple(int(a - b) for a, b in zip(T, src))
+            K = _p2p_kernel_g0(N, S, off).reshape(FIELDS * S ** 3, S ** 3)
+            near[T] += (K @ ml[src]).reshape(FIELDS, S ** 3)
+    mesh = mesh_of(np.moveaxis(far + near, 3, 0), S)
+    return mesh[0], mesh[1:]
+
+
+# --------------------------------------------------------------- eq. gerr
+def gf_error(g_fmm_p, g_pm_p, g_fmm_np, g_pm_np):
+    """Eq. gerr: the per-cell magnitude of g_FMM^P - g_PM^P - (g_FMM^NP -
+    g_PM^NP) (arrays (3, N, N, N)); returns (L_MAX, L2 = root mean square)."""
+    d = (np.asarray(g_fmm_p) - np.asarray(g_pm_p)) - (np.asarray(g_fmm_np) - np.asarray(g_pm_np))
+    mag = np.sqrt(np.sum(d * d, axis=0))
+    return float(mag.max()), float(np.sqrt(np.mean(mag * mag)))
+
+
+def me_error(g_fmm_np, g_pm_np):
+    """The multipole-expansion error of the isolated problem (L_MAX, L2)."""
+    d = np.asarray(g_fmm_np) - np.asarray(g_pm_np)
+    mag = np.sqrt(np.sum(d * d, axis=0))
+    return float(mag.max()), float(np.sqrt(np.mean(mag * mag)))
+
