@@ -93,6 +93,41 @@ def test_m2m_after_p2m_equals_p2m_to_the_parent(p):
     np.testing.assert_allclose(fmm.m2m(M3, p), fmm.p2m(m, 2, p), atol=1e-14 * np.abs(M3).max())
 
 
+@pytest.mark.parametrize("p", [2, 4, 6, 8])
+def test_l2l_and_l2p_reproduce_polynomials_below_the_order(p):
+    # eq. fmm3 with T^T interpolates the parent's local field at the child
+    # points (and L2P at the cell centres): any polynomial of degree < p per
+    # axis, sampled at the parent gridlet points, is reproduced exactly
+    rng = np.random.default_rng(p)
+    coef = rng.standard_normal((p, p, p))
+    def poly(pts):        # pts (k, 3) as (x, y, z), node-size units about the parent centre
+        out = np.zeros(len(pts))
+        for a in range(p):
+            for b in range(p):
+                for c in range(p):
+                    out += coef[a, b, c] * pts[:, 0] ** a * pts[:, 1] ** b * pts[:, 2] ** c
+        return out
+    parent = fmm.tensor_points(fmm.gridlet_offsets(p))
+    Fp = poly(parent)[None, :]                                       # one field
+    for child in [(0, 0, 0), (1, 0, 1), (1, 1, 1)]:
+        got = fmm.l2l(Fp, p, child)[0]
+        pts = fmm.tensor_points(fmm.gridlet_offsets(p)) / 2.0 + (np.array(child) - 0.5) / 2.0
+        np.testing.assert_allclose(got, poly(pts), atol=1e-10 * np.abs(Fp).max())
+    S = 2 * p
+    cells = fmm.tensor_points((np.arange(S) + 0.5) / S - 0.5)
+    np.testing.assert_allclose(Fp[0] @ fmm.l2p_matrix(S, p).T, poly(cells), atol=1e-10 * np.abs(Fp).max())
+
+
+def test_mean_potential_vanishes_for_a_mean_free_field():
+    # the k = 0 mode is removed (Sec. 1): the FMM potential of a mean-free
+    # field has (nearly) zero mean, to the truncation of the expansion
+    rho = inputs.lognormal(16, sigma=0.8, seed=11)
+    phi, _ = fmm.solve(rho, 2, 4)
+    p_ref, _ = _pm_s1(rho)
+    assert abs(phi.mean() - p_ref.mean()) < 1e-12 * np.abs(p_ref).max()
+    assert abs(p_ref.mean()) < 1e-3 * np.abs(p_ref).max()
+
+
 def test_interaction_zone_sizes_and_translation_invariance():
     assert len(fmm.interaction_list(2, (0, 0, 0))) == 37
     for lev in (3, 4):
