@@ -126,7 +126,7 @@ struct Plan {
 // plan creation, never inside a solve, so a solve is safe to capture.
 cudaError_t setup_upward(const Plan& P);
 // Levels whose local field is kept in FP64 (M2L output reduced in FP64, L2L
-// from them in FP64): the two coarse levels, and at high order every level
+// from them in double-float): the two coarse levels, and at high order every level
 // above the leaves.
 inline bool wide_level(const Plan& P, int l) { return l <= kExtTopLevel || (P.p >= kWideOrder && l < P.L); }
 // First level of the tensor-core M2L in the mixed forms.
