@@ -440,7 +440,8 @@ def run_batch(args):
     Ns = [int(x) for x in rng.choice([32, 48, 64, 96, 128], nf)]
     ps = [int(x) for x in rng.choice([4, 6], nf)]
     sig = rng.uniform(0.3, 1.5, nf)
-    os.environ.setdefault("FMM_AUTOTUNE_CACHE", os.path.join(ROOT, "gpurun_out", "autotune.jsonl"))
+    import tempfile
+    os.environ.setdefault("FMM_AUTOTUNE_CACHE", os.path.join(tempfile.gettempdir(), "fmm_autotune.jsonl"))
     t0 = time.perf_counter()
     batch = B.Batch(Ns, [0] * nf, ps, precision=B.FMM_PREC_BF16X3)
     tune_s = time.perf_counter() - t0
