@@ -53,7 +53,7 @@ def gaussian_field_torch(n, rng, device, slope=-2.0):
     del kx, ky, kz, k
     g = torch.fft.ifftn(torch.fft.fftn(white) * amp).real
     g -= g.mean()
-    s = g.std()
+    s = g.std(unbiased=False)          # population deviation, as numpy's std
     return g / s if float(s) > 0 else g
 
 
