@@ -44,7 +44,7 @@ def _rank(rank, ws, port, out):
 def test_two_replicas_time_as_the_slowest_and_solve_distinct_fields():
     ws = 2
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:       # no fork of a threaded process
         out = mgr.dict()
         mp.spawn(_rank, args=(ws, port, out), nprocs=ws, join=True)
         res = dict(out)
