@@ -187,6 +187,30 @@ def accuracy_vs_pm(rho, phi, acc):
             "note": "relative L2 over all cells; PM(G_S1) is the primary reference (same G in PM and FMM)"}
 
 
+def learned_correction(args):
+    """The learned table correction the headline workload applies: the
+    shipped order-6 weights (or --correction) in the tensor-core forms,
+    None otherwise.  The weights file path is under "path"."""
+    wpath = args.correction or (DEFAULT_CORRECTION if args.p == 6 else None)
+    if args.precision == "fp32" or args.no_correction or not wpath or not os.path.exists(wpath):
+        return None
+    here = os.path.dirname(os.path.abspath(__file__))
+    return {"path": wpath, "weights": os.path.relpath(wpath, here), "inference": "bf16",
+            "applied_to": "M2L tables, levels 2..L"}
+
+
+def headline_config(args, learned, ws):
+    """The `config` object of the headline workload; both arms print it."""
+    n, L, p = args.n, args.L, args.p
+    return {"workload": f"{n}^3 lognormal sigma=0.5 (seeded), order p={p}, L={L} (S={n >> L}), "
+                        f"M2L levels>=4 {args.precision}, levels 2-3 extended-precision CUDA-core"
+                        + (", learned table correction" if learned else ""),
+            "N": n, "L": L, "order": p, "precision": args.precision,
+            "learned_correction": None if learned is None else {k: v for k, v in learned.items() if k != "path"},
+            "l2_flush": "256 MB buffer written between timed steps",
+            "parallelism": f"replicas x{ws}"}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -203,13 +227,13 @@ def run_reference(args):
         times.append(time.perf_counter() - t)
     ms = 1000.0 * statistics.mean(times)
     value = n ** 3 / (ms / 1000.0)
-    sample = (f"FP64 numpy oracle, full solve of a {n}^3 lognormal field per step with order p={p} and leaf "
-              f"size S=8 (L={L}), host cores")
+    sample = (f"FP64 numpy oracle (plain method, no correction), full solve of a {n}^3 lognormal sigma=0.5 "
+              f"field per step with order p={p} and the workload's leaf size S=8 (L={L}); cells/s of the "
+              f"sample stand for the {args.n}^3 workload")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"oracle sample: {n}^3 lognormal sigma=0.5, p={p}, L={L}", "N": n, "L": L,
-                       "order": p},
+            "config": headline_config(args, learned_correction(args), ws),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -320,13 +344,10 @@ def run_ours(args):
     plan = B.Plan(n, L, p)
     if tc:
         plan.set_precision(prec)
-    learned = None
-    wpath = args.correction or (DEFAULT_CORRECTION if p == 6 else None)
-    if tc and not args.no_correction and wpath and os.path.exists(wpath):
-        w = torch.from_numpy(np.load(wpath)["w"].astype(np.float32)).to(dev)
+    learned = learned_correction(args)
+    if learned is not None:
+        w = torch.from_numpy(np.load(learned["path"])["w"].astype(np.float32)).to(dev)
         B.fmm_plan_set_correction(plan.handle, w)   # tabulated once at plan time; BF16 inference
-        learned = {"weights": os.path.relpath(wpath, os.path.dirname(os.path.abspath(__file__))),
-                   "inference": "bf16", "applied_to": "M2L tables, levels 2..L"}
     with ClockSampler(dev.index) as clk:
         step_ms, stage, wall = _time_solves(B, plan, rho, phi, acc, args.steps, args.warmup, l2_flush, stream,
                                             barrier)
@@ -400,12 +421,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if not tc else ("bf16x3" if prec == B.FMM_PREC_BF16X3 else "bf16"),
         "data": "synthetic",
-        "config": {"workload": f"{n}^3 lognormal sigma=0.5 (seeded), order p={p}, L={L} (S={n >> L}), "
-                               f"M2L levels>=4 {args.precision}, levels 2-3 extended-precision CUDA-core"
-                               + (", learned table correction" if learned else ""),
-                   "N": n, "L": L, "order": p, "precision": args.precision, "learned_correction": learned,
-                   "l2_flush": "256 MB buffer written between timed steps",
-                   "parallelism": f"replicas x{ws}"},
+        "config": headline_config(args, learned, ws),
         "stage_ms": stage_ms,
         "wall_s": wall,
         "roofline": roof,
