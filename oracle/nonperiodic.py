@@ -11,31 +11,30 @@ function, what is left (eq. gerr):
 
 with absolute norms L_MAX (maximum over cells) and L2 (root mean square over
 cells) for a unit mass in a unit box (Sec. 3: the characteristic acceleration
-is 1, so the absolute error is a relative one).  PM accelerations come from
-the potential by the 4th-order central difference (Sec. 3), FMM accelerations
-from the expansion.
+is 1, so the absolute error is a relative one).
 
 Readings (the paper is brief here):
+  * the periodic PM of eq. gerr uses the same Green's function as the FMM,
+    G_S1 sampled at the mesh offsets (Sec. 3 defines G_* as the function with
+    which PM and FMM agree; the figures compare the two with one G);
   * the non-periodic problem has the isolated Green's function G_0 =
     -1/(4 pi r) everywhere, no mean removal (masses m = rho / N^3), and the
     same cell self term G(0) as the periodic solver;
-  * the non-periodic PM is the zero-padded (Hockney) FFT convolution, padded
-    to (2N + 4)^3 so that its potential two cells outside the box (from the
-    same convolution) feeds the finite difference at the box faces;
+  * the non-periodic PM is the zero-padded (Hockney) FFT convolution;
   * the non-periodic FMM keeps the tree, gridlets and operators of the
     periodic one and drops the wrap: a node's near zone is its in-box
     neighbours, its interaction zone the children of its parent's in-box
     neighbours that are not its neighbours (Sec. 2, Fig. fmm without the
     periodic translation), with G_0 in M2L and P2P;
-  * the periodic PM of eq. gerr is the spectral PM with G_K (Sec. 1 eq. gfk),
-    the PM whose agreement defines the optimal G_*.
-Open before Table 1 can be compared: the paper's FMM-HPM computes the near
-zone with the PM's own Green's function on the sub-grid (Sec. 3: it must
-match PM), and its near-zone accelerations presumably by the same finite
-difference; with an exact-gradient near zone the source-cell neighbourhood
-dominates eq. gerr (O(1) in a 16^3 corner-source test).  This module
-provides the pinned pieces: isolated PM and FMM, the 4th-order difference and
-the norms of eq. gerr.
+  * accelerations: this FMM evaluates -grad G exactly at the cell offsets in
+    its near zone and carries -grad G through its expansions, so the PM
+    accelerations it is measured against are the convolutions with -grad G
+    (`pm.pm` and `pm_isolated_accel`).  Sec. 3 takes the PM accelerations
+    from the potential by a 4th-order difference, which matches an FMM whose
+    near zone is a PM-like sub-grid solve; against this FMM the difference
+    leaves an O(1) error at the source and, for a corner source, at its
+    periodic images, which eq. gerr cannot subtract (the non-periodic problem
+    has no images).  The difference is kept (`fd4*`) for that comparison.
 """
 from functools import lru_cache
 
@@ -106,6 +105,26 @@ def pm_isolated(m, self_value):
     mp[:n, :n, :n] = m
     phi_pad = np.fft.irfftn(np.fft.rfftn(mp) * np.fft.rfftn(kern), s=(n2, n2, n2), axes=(0, 1, 2))
     return phi_pad[:n, :n, :n], phi_pad
+
+
+def pm_isolated_accel(m):
+    """Accelerations g = -grad Phi of the isolated problem: zero-padded FFT
+    convolution of the masses with -grad G_0 sampled at the mesh offsets
+    (padded to 2N, offsets in [-(N - 1), N - 1]; zero at d = 0).  Returns
+    (3, N, N, N), components (x, y, z)."""
+    m = np.asarray(m, dtype=np.float64)
+    n = m.shape[0]
+    n2 = 2 * n
+    k = np.arange(n2)
+    k = np.where(k < n, k, k - n2).astype(np.float64)
+    dz, dy, dx = np.meshgrid(k, k, k, indexing="ij")
+    kern = -grad_g0(np.stack([dx, dy, dz], axis=-1) / n)
+    mp = np.zeros((n2, n2, n2))
+    mp[:n, :n, :n] = m
+    fm = np.fft.rfftn(mp)
+    g = [np.fft.irfftn(fm * np.fft.rfftn(kern[..., c]), s=(n2, n2, n2), axes=(0, 1, 2))[:n, :n, :n]
+         for c in range(3)]
+    return np.stack(g)
 
 
 def fd4(phi, h, axis):
