@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "fmm_internal.cuh"
+#include "green_s1.cuh"
 #include "mlp.cuh"
 
 namespace fmm {
@@ -333,29 +334,16 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
 // ------------------------------------------------- mesh Green's function
 // G_S1 and -grad G_S1 at the periodic mesh offsets d/N, d in [0, N)^3, with
 // the cell self term at d = 0 (for the PM target, Sec. 3 eq. pmconv).
-__device__ inline double xi(double t) {
-  return (9.0 / (8.0 * 3.14159265358979323846)) * sinpi(t) - (1.0 / (24.0 * 3.14159265358979323846)) * sinpi(3.0 * t);
-}
-__device__ inline double dxi(double t) { return 1.125 * cospi(t) - 0.125 * cospi(3.0 * t); }
-
 __global__ void k_mesh_green(int N, float* __restrict__ out) {
   const size_t n3 = (size_t)N * N * N;
-  const double inv4pi = 1.0 / (4.0 * 3.14159265358979323846);
+  const double inv4pi = 1.0 / (4.0 * green::kPi);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
     const int ix = (int)(i % N), iy = (int)((i / N) % N), iz = (int)(i / ((size_t)N * N));
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-    if (ix | iy | iz) {
-      const double x = (double)ix / N, y = (double)iy / N, z = (double)iz / N;
-      const double hx = xi(x), hy = xi(y), hz = xi(z);
-      const double r2 = hx * hx + hy * hy + hz * hz, r = sqrt(r2);
-      v[0] = -inv4pi / r;
-      const double c = -inv4pi / (r2 * r);
-      v[1] = c * hx * dxi(x);
-      v[2] = c * hy * dxi(y);
-      v[3] = c * hz * dxi(z);
-    } else {
-      v[0] = -(3.0 * log(2.0 + sqrt(3.0)) - 0.5 * 3.14159265358979323846) * N * inv4pi;
-    }
+    if (ix | iy | iz)
+      green::gs1((double)ix / N, (double)iy / N, (double)iz / N, v);
+    else
+      v[0] = -green::cube_mean_inv_r() * N * inv4pi;
     for (int f = 0; f < 4; ++f) out[f * n3 + i] = (float)v[f];
   }
 }
