@@ -282,6 +282,41 @@ const char* fmm_error_string(int code);
 int fmm_plan_copy_stage(fmm_plan* plan, int stage, int level, float* dst,
                         size_t count, void* stream);
 
+/* ---- error of a result against PM ---------------------------------------- */
+
+/* Relative L2 error of a solution against the PM solution with the same
+ * Green's function, over sampled cells.  Sec. 3 defines the optimal G_* as
+ * the function with which PM and FMM give the same potential; PM is the
+ * periodic convolution of the masses m = (rho - mean rho) / N^3 with G_S1
+ * sampled at the mesh offsets d/N (eq. pmconv), and with the plan's self
+ * term G(0) at d = 0.  At each sampled cell that convolution is evaluated
+ * exactly, as a direct sum over all N^3 source cells (per-pair G_S1 in FP32,
+ * sums in FP64: about 1e-7 relative), and compared with the given values.
+ * The reference is always the plain G_S1, whatever precision mode or
+ * learned correction the plan has, so that every form's error is stated
+ * against the same target.
+ *   plan        the plan (its N; its mean scratch is overwritten).
+ *   density     device, N^3 floats, [z][y][x] (x fastest), read only.
+ *   potential   device, N^3 floats, the result to assess.
+ *   accel       device, 3 N^3 floats (SoA ax | ay | az), the result to assess.
+ *   samples     1 .. 1024 target cells: the first `samples` outputs of
+ *               splitmix64 seeded with `seed`, each modulo N^3 (a cell index
+ *               x + N (y + N z); drawn with replacement).
+ *   seed        generator seed.
+ *   out         host, 2 doubles, written: out[0] = ||dPhi|| / ||Phi_PM||,
+ *               out[1] = ||dg|| / ||g_PM|| (all three components) over the
+ *               sampled cells.
+ *   stream      cudaStream_t as void*.  The call is synchronous: it returns
+ *               after the work it enqueued on `stream` has finished.
+ * Cost: samples x N^3 pair evaluations; scratch of up to 10 MB is allocated
+ * and freed by the call.  Do not run it concurrently with a solve of the
+ * same plan.
+ * Returns FMM_OK, FMM_ERR_ARG (NULL or misaligned pointers, samples out of
+ * range), FMM_ERR_ALLOC or FMM_ERR_CUDA. */
+int fmm_plan_error_stats(fmm_plan* plan, const float* density, const float* potential,
+                         const float* accel, int samples, unsigned long long seed,
+                         double* out, void* stream);
+
 /* ---- allocation-free entry point ----------------------------------------- */
 
 /* Mean of a device float array, without any allocation by the library.  The

@@ -70,6 +70,8 @@ SIGNATURES = {
     "fmm_batch_destroy": (None, [_VP]),
     "fmm_autotune_levels": (_I, [_I, _I, _I, ctypes.c_char_p, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
     "fmm_plan_stage_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), _I]),
+    "fmm_plan_error_stats": (_I, [_VP, _FP, _FP, _FP, _I, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_double),
+                                  _VP]),
 }
 
 FMM_TIME_MEAN, FMM_TIME_P2M, FMM_TIME_M2M, FMM_TIME_M2L, FMM_TIME_L2L, FMM_TIME_P2P = range(6)
@@ -126,6 +128,15 @@ def fmm_plan_destroy(plan):
 def fmm_solve(plan, density, potential, accel, stream=None):
     _check(lib().fmm_solve(plan, density.data_ptr(), potential.data_ptr(), accel.data_ptr(),
                            _stream_of(density, stream)), "fmm_solve")
+
+
+def fmm_plan_error_stats(plan, density, potential, accel, samples=256, seed=0, stream=None):
+    """(relative L2 of the potential, of the acceleration) against the PM
+    solution with G_S1, over `samples` sampled cells.  Synchronous."""
+    out = (ctypes.c_double * 2)()
+    _check(lib().fmm_plan_error_stats(plan, density.data_ptr(), potential.data_ptr(), accel.data_ptr(), int(samples),
+                                      int(seed), out, _stream_of(density, stream)), "fmm_plan_error_stats")
+    return out[0], out[1]
 
 
 def fmm_solve_host(plan, density, potential, accel, stream=None):
@@ -280,6 +291,9 @@ class Plan:
             accel = torch.empty((3, n, n, n), dtype=torch.float32, device=density.device)
         fmm_solve(self.handle, density, potential, accel, stream)
         return potential, accel
+
+    def error_stats(self, density, potential, accel, samples=256, seed=0, stream=None):
+        return fmm_plan_error_stats(self.handle, density, potential, accel, samples, seed, stream)
 
     def stage(self, stage, level):
         import torch

@@ -1,5 +1,6 @@
 // The C-ABI of libfmm: plan lifecycle, solve orchestration and errors.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -555,6 +556,47 @@ int fmm_plan_copy_stage(fmm_plan* plan, int stage, int level, float* dst, size_t
   }
   if (count < need) return set_err(FMM_ERR_ARG);
   FMM_CUDA_TRY(cudaMemcpyAsync(dst, src, need * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return set_err(FMM_OK);
+}
+
+int fmm_plan_error_stats(fmm_plan* plan, const float* density, const float* potential, const float* accel,
+                         int samples, unsigned long long seed, double* out, void* stream) {
+  if (!plan || !density || !potential || !accel || !out) return set_err(FMM_ERR_ARG);
+  if (!aligned16(density) || !aligned16(potential) || !aligned16(accel)) return set_err(FMM_ERR_ARG);
+  if (samples < 1 || samples > fmm::error_stats_max_samples()) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const unsigned long long n3 = (unsigned long long)P.N * P.N * P.N;
+  std::vector<unsigned long long> targets((size_t)samples);
+  for (int i = 0; i < samples; ++i) {
+    // output i of splitmix64 (Steele, Lea and Flood 2014) seeded with `seed`
+    unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    z ^= z >> 31;
+    targets[(size_t)i] = z % n3;
+  }
+  struct Scratch {
+    unsigned long long* targets = nullptr;
+    double* partials = nullptr;
+    double* sums = nullptr;
+    ~Scratch() {
+      cudaFree(targets);
+      cudaFree(partials);
+      cudaFree(sums);
+    }
+  } d;
+  const size_t np = (size_t)fmm::error_stats_grid_x(P, samples) * samples * 4;
+  if (!dev_alloc(&d.targets, (size_t)samples) || !dev_alloc(&d.partials, np) || !dev_alloc(&d.sums, 4))
+    return set_err(FMM_ERR_ALLOC);
+  FMM_CUDA_TRY(cudaMemcpyAsync(d.targets, targets.data(), sizeof(unsigned long long) * samples,
+                               cudaMemcpyHostToDevice, s));
+  FMM_CUDA_TRY(fmm::launch_error_stats(P, density, potential, accel, d.targets, samples, d.partials, d.sums, s));
+  double sums[4] = {0.0, 0.0, 0.0, 0.0};
+  FMM_CUDA_TRY(cudaMemcpyAsync(sums, d.sums, sizeof(sums), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA_TRY(cudaStreamSynchronize(s));
+  out[0] = sums[1] > 0.0 ? std::sqrt(sums[0] / sums[1]) : std::sqrt(sums[0]);
+  out[1] = sums[3] > 0.0 ? std::sqrt(sums[2] / sums[3]) : std::sqrt(sums[2]);
   return set_err(FMM_OK);
 }
 

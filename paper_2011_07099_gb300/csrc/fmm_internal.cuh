@@ -159,6 +159,14 @@ int mlp_backward_blocks(const Plan& P);
 cudaError_t launch_adam(float* w, const float* g, float* m, float* v, size_t n, int step, float lr, float b1, float b2,
                         float eps, cudaStream_t s);
 cudaError_t launch_mesh_green(int N, float* out, int sms, cudaStream_t s);
+// Sampled error against the direct periodic sum with G_S1 (errstats.cu):
+// targets T <= error_stats_max_samples(), partials error_stats_grid_x(P, T)
+// x T x 4 doubles, sums 4 doubles.
+int error_stats_max_samples();
+int error_stats_grid_x(const Plan& P, int T);
+cudaError_t launch_error_stats(Plan& P, const float* rho, const float* phi, const float* acc,
+                               const unsigned long long* targets, int T, double* partials, double* sums,
+                               cudaStream_t s);
 cudaError_t launch_tab_bf16(Plan& P, int level, cudaStream_t s);
 cudaError_t launch_split_bf16(Plan& P, int level, cudaStream_t s);
 cudaError_t launch_m2l_tc(Plan& P, int level, int mode, cudaStream_t s);
