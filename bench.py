@@ -6,7 +6,9 @@ L2P and the near-zone sum) of a seeded synthetic 256^3 density field,
 order p = 6, with the input already resident in HBM.  The timed form is the
 mixed-precision one (tensor-core bf16x3 M2L at levels >= 4); the plain FP32
 form is timed on the same field in the same run, and the result's error
-against PM is stated.  Prints ONE JSON line.
+against PM is stated twice: by the library (fmm_plan_error_stats, exact at
+1024 sampled cells) and, with the CPU baseline, over every cell by the FP64
+oracle's FFT PM.  Prints ONE JSON line.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
                     [--n 256 --L 5 --p 6 --precision fp32|bf16|bf16x3]
@@ -355,6 +357,10 @@ def run_ours(args):
     value = whole_job_cells_per_s(ws, n, ms)
     result_phi = phi.cpu().numpy() if (rank == 0 and ws == 1 and not args.no_cpu_baseline) else None
     result_acc = acc.cpu().numpy() if result_phi is not None else None
+    # the library's own statement of this result's error against PM with
+    # G_S1, measured exactly at sampled cells (outside the timed region)
+    stmt_cells = 1024
+    stmt = plan.error_stats(rho, phi, acc, samples=stmt_cells, seed=1)
 
     # per-stage means over the timed steps
     nslot = len(stage[0])
@@ -432,6 +438,8 @@ def run_ours(args):
         "gpu_launches": launches_per_solve(L, tc, p) * args.steps,
         "solve_roofline": solve_roofline(n, L, p, tc, ms, peaks),
         "clocks": clocks,
+        "error_statement": {"vs_pm_gs1": {"phi": stmt[0], "g": stmt[1]}, "cells": stmt_cells,
+                            "source": "fmm_plan_error_stats (exact direct sum at sampled cells, GPU)"},
     }
     if plain is not None:
         line["plain_fp32"] = plain
