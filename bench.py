@@ -360,7 +360,12 @@ def run_ours(args):
     # the library's own statement of this result's error against PM with
     # G_S1, measured exactly at sampled cells (outside the timed region)
     stmt_cells = 1024
-    stmt = plan.error_stats(rho, phi, acc, samples=stmt_cells, seed=1)
+    try:
+        e_phi, e_g = plan.error_stats(rho, phi, acc, samples=stmt_cells, seed=1)
+        statement = {"vs_pm_gs1": {"phi": e_phi, "g": e_g}, "cells": stmt_cells,
+                     "source": "fmm_plan_error_stats (exact direct sum at sampled cells, GPU)"}
+    except B.FMMError as e:   # reported in the line; the timed numbers stand
+        statement = {"failed": str(e)}
 
     # per-stage means over the timed steps
     nslot = len(stage[0])
@@ -438,8 +443,7 @@ def run_ours(args):
         "gpu_launches": launches_per_solve(L, tc, p) * args.steps,
         "solve_roofline": solve_roofline(n, L, p, tc, ms, peaks),
         "clocks": clocks,
-        "error_statement": {"vs_pm_gs1": {"phi": stmt[0], "g": stmt[1]}, "cells": stmt_cells,
-                            "source": "fmm_plan_error_stats (exact direct sum at sampled cells, GPU)"},
+        "error_statement": statement,
     }
     if plain is not None:
         line["plain_fp32"] = plain
