@@ -75,3 +75,24 @@ def test_setters_validate_before_touching_the_device(lib):
                  lambda: L.fmm_plan_error_stats(None, None, None, None, 16, 0, None, None)):
         assert call() == binding.FMM_ERR_ARG
         assert L.fmm_last_error() == binding.FMM_ERR_ARG
+
+
+def test_batch_and_autotuner_validate_before_touching_the_device(lib):
+    import ctypes
+    L = binding.lib()
+    ints = lambda *v: (ctypes.c_int * len(v))(*v)
+    assert not L.fmm_batch_create(0, ints(32), ints(3), ints(4))
+    assert L.fmm_last_error() == binding.FMM_ERR_ARG
+    assert not L.fmm_batch_create(1, None, ints(3), ints(4))
+    assert L.fmm_last_error() == binding.FMM_ERR_ARG
+    # the first field's shape is invalid (30 is not a multiple of 2^3)
+    assert not L.fmm_batch_create(1, ints(30), ints(3), ints(4))
+    assert L.fmm_last_error() == binding.FMM_ERR_ARG
+    for call in (lambda: L.fmm_batch_set_precision(None, 0), lambda: L.fmm_batch_get_levels(None, None),
+                 lambda: L.fmm_batch_solve(None, None, None, None, None), lambda: L.fmm_batch_check(None)):
+        assert call() == binding.FMM_ERR_ARG
+    out_L, out_ms = ctypes.c_int(), ctypes.c_float()
+    assert L.fmm_autotune_levels(2, 4, 0, None, ctypes.byref(out_L), ctypes.byref(out_ms)) == binding.FMM_ERR_ARG
+    assert L.fmm_autotune_levels(64, 0, 0, None, ctypes.byref(out_L), ctypes.byref(out_ms)) == binding.FMM_ERR_ARG
+    assert L.fmm_autotune_levels(64, 4, 0, None, None, ctypes.byref(out_ms)) == binding.FMM_ERR_ARG
+    L.fmm_batch_destroy(None)
