@@ -83,7 +83,11 @@ void fmm_plan_destroy(fmm_plan* plan);
  * (37 periodic nodes at level 2, 189 below) with G_S1, L2L down the tree,
  * and at each leaf L2P plus the direct near-zone sum over its 27 periodic
  * neighbour leaves.  Buffers must not overlap.  Returns FMM_ERR_ARG for NULL
- * or misaligned pointers, FMM_ERR_CUDA if a launch fails. */
+ * or misaligned pointers, FMM_ERR_CUDA if a launch fails.  The return value
+ * covers the enqueueing only: a bounded device-side wait of the tensor-core
+ * M2L that runs out (fmm_plan_set_timeout_ms) is recorded in the plan's
+ * device error word, so the outputs are valid only once fmm_plan_check()
+ * has returned FMM_OK after the solve. */
 int fmm_solve(fmm_plan* plan, const float* density, float* potential,
               float* accel, void* stream);
 
@@ -112,8 +116,10 @@ int fmm_plan_set_precision(fmm_plan* plan, int mode);
 
 /* Limit of every bounded device-side wait (pipeline barriers of the
  * tensor-core M2L), in milliseconds, 1..600000; default 2000.  A wait that
- * runs out makes its kernel skip the rest of its work, free its tensor
- * memory and return; fmm_plan_check() then reports FMM_ERR_TIMEOUT. */
+ * runs out makes its kernel skip the rest of its work, wait (bounded) for the
+ * copies and MMAs it already issued, free its tensor memory and return;
+ * fmm_plan_check() then reports FMM_ERR_TIMEOUT and the outputs of that solve
+ * are not valid. */
 int fmm_plan_set_timeout_ms(fmm_plan* plan, int ms);
 
 /* Test hook for the failure path (no GPU fault is involved):
@@ -128,15 +134,6 @@ int fmm_plan_inject_fault(fmm_plan* plan, int kind);
  * CUDA cores.  Smaller is more accurate, larger is faster; default 2.
  * FMM_ERR_ARG outside 1..189. */
 int fmm_plan_set_m2l_group(fmm_plan* plan, int offsets_per_partial);
-
-/* Tensor-core M2L: number of CTAs (1, 2 or 4) launched as one thread-block
- * cluster along the target tiles.  They share a row tile and a child type,
- * hence the same translation tiles, which each copies 1/ctas of and
- * multicasts to the others: the L2 traffic of those tiles falls by that
- * factor.  Levels whose target-tile count is not a multiple run without
- * clusters.  Results do not depend on it.  Default 2.  FMM_ERR_ARG
- * otherwise. */
-int fmm_plan_set_m2l_cluster(fmm_plan* plan, int ctas);
 
 /* Mixed-precision forms: the first tree level whose M2L (eq. fmm2) runs on
  * the tensor cores; coarser levels run the FP32 CUDA-core kernel.  Default
@@ -310,8 +307,9 @@ int fmm_plan_copy_stage(fmm_plan* plan, int stage, int level, float* dst,
  *               after the work it enqueued on `stream` has finished.
  * Cost: samples x N^3 pair evaluations (on one GB300 0.14 s for 512 samples
  * at 256^3, 0.27 s for 1024); scratch of up to 10 MB is allocated and freed
- * by the call.  Do not run it concurrently with a solve of the
- * same plan.
+ * by the call; the statement's density mean goes to that scratch too, so
+ * the plan's mean stage (FMM_STAGE_MEAN) still holds the last solve's.  Do
+ * not run it concurrently with a solve of the same plan.
  * Returns FMM_OK, FMM_ERR_ARG (NULL or misaligned pointers, samples out of
  * range), FMM_ERR_ALLOC or FMM_ERR_CUDA. */
 int fmm_plan_error_stats(fmm_plan* plan, const float* density, const float* potential,
@@ -338,7 +336,8 @@ int fmm_plan_error_stats(fmm_plan* plan, const float* density, const float* pote
  * (different streams, or different host threads on one device) race and must
  * be serialised by the caller.  The first call on each device looks up the
  * array's device address with that device current (a one-time set-up); make
- * that first call before any stream capture.
+ * that first call before any stream capture.  Host threads may make their
+ * first calls concurrently: the looked-up address is published atomically.
  * Returns FMM_OK, FMM_ERR_ARG (NULL pointers, count 0 or above the maximum),
  * FMM_ERR_UNSUPPORTED (device ordinal >= 64) or FMM_ERR_CUDA. */
 int fmm_mean_density_noalloc(const float* density, size_t count, double* mean, void* stream);

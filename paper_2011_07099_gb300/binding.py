@@ -51,7 +51,6 @@ SIGNATURES = {
     "fmm_plan_set_timing": (_I, [_VP, _I]),
     "fmm_plan_check": (_I, [_VP]),
     "fmm_plan_set_m2l_group": (_I, [_VP, _I]),
-    "fmm_plan_set_m2l_cluster": (_I, [_VP, _I]),
     "fmm_plan_set_tc_min_level": (_I, [_VP, _I]),
     "fmm_plan_set_timeout_ms": (_I, [_VP, _I]),
     "fmm_plan_inject_fault": (_I, [_VP, _I]),
@@ -159,10 +158,6 @@ def fmm_plan_get_shape(plan):
 def fmm_plan_copy_stage(plan, stage, level, dst, stream=None):
     _check(lib().fmm_plan_copy_stage(plan, int(stage), int(level), dst.data_ptr(), dst.numel(),
                                      _stream_of(dst, stream)), "fmm_plan_copy_stage")
-
-
-def fmm_plan_set_m2l_cluster(plan, ctas):
-    _check(lib().fmm_plan_set_m2l_cluster(plan, int(ctas)), "fmm_plan_set_m2l_cluster")
 
 
 def fmm_plan_set_m2l_group(plan, offsets_per_partial):

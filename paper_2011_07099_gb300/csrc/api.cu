@@ -332,12 +332,6 @@ int fmm_plan_inject_fault(fmm_plan* plan, int kind) {
   return set_err(FMM_OK);
 }
 
-int fmm_plan_set_m2l_cluster(fmm_plan* plan, int ctas) {
-  if (!plan || (ctas != 1 && ctas != 2 && ctas != 4)) return set_err(FMM_ERR_ARG);
-  reinterpret_cast<Plan*>(plan)->tc_cluster = ctas;
-  return set_err(FMM_OK);
-}
-
 int fmm_plan_set_m2l_group(fmm_plan* plan, int offsets_per_partial) {
   if (!plan || offsets_per_partial < 1 || offsets_per_partial > fmm::kMaxOffsets) return set_err(FMM_ERR_ARG);
   reinterpret_cast<Plan*>(plan)->tc_group = offsets_per_partial;
@@ -580,18 +574,22 @@ int fmm_plan_error_stats(fmm_plan* plan, const float* density, const float* pote
     unsigned long long* targets = nullptr;
     double* partials = nullptr;
     double* sums = nullptr;
+    double* mean = nullptr;
     ~Scratch() {
       cudaFree(targets);
       cudaFree(partials);
       cudaFree(sums);
+      cudaFree(mean);
     }
   } d;
   const size_t np = (size_t)fmm::error_stats_grid_x(P, samples) * samples * 4;
-  if (!dev_alloc(&d.targets, (size_t)samples) || !dev_alloc(&d.partials, np) || !dev_alloc(&d.sums, 4))
+  if (!dev_alloc(&d.targets, (size_t)samples) || !dev_alloc(&d.partials, np) || !dev_alloc(&d.sums, 4) ||
+      !dev_alloc(&d.mean, (size_t)P.n_partials + 1))
     return set_err(FMM_ERR_ALLOC);
   FMM_CUDA_TRY(cudaMemcpyAsync(d.targets, targets.data(), sizeof(unsigned long long) * samples,
                                cudaMemcpyHostToDevice, s));
-  FMM_CUDA_TRY(fmm::launch_error_stats(P, density, potential, accel, d.targets, samples, d.partials, d.sums, s));
+  FMM_CUDA_TRY(
+      fmm::launch_error_stats(P, density, potential, accel, d.targets, samples, d.partials, d.sums, d.mean, s));
   double sums[4] = {0.0, 0.0, 0.0, 0.0};
   FMM_CUDA_TRY(cudaMemcpyAsync(sums, d.sums, sizeof(sums), cudaMemcpyDeviceToHost, s));
   FMM_CUDA_TRY(cudaStreamSynchronize(s));

@@ -156,13 +156,14 @@ int error_stats_grid_x(const Plan& P, int T) {
 
 cudaError_t launch_error_stats(Plan& P, const float* rho, const float* phi, const float* acc,
                                const unsigned long long* targets, int T, double* partials, double* sums,
-                               cudaStream_t s) {
-  cudaError_t e = launch_mean(P, rho, s);
+                               double* mean_scratch, cudaStream_t s) {
+  double* mean = mean_scratch + P.n_partials;
+  cudaError_t e = launch_mean_into(P, rho, mean_scratch, mean, s);
   if (e != cudaSuccess) return e;
   const int gx = error_stats_grid_x(P, T);
   const dim3 grid(gx, (T + kEsThreads - 1) / kEsThreads);
   const size_t smem = sizeof(double) * kEsChunk + 2 * sizeof(float) * (size_t)P.N;
-  k_es_direct<<<grid, kEsThreads, smem, s>>>(rho, P.d_mean, P.N, targets, T, partials);
+  k_es_direct<<<grid, kEsThreads, smem, s>>>(rho, mean, P.N, targets, T, partials);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t n3 = (size_t)P.N * P.N * P.N;

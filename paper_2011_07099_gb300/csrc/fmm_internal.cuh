@@ -94,7 +94,6 @@ struct Plan {
   void* Apre[kMaxLevel + 1] = {};          // precomputed split translation tiles per offset slot
   int tc_group = 2;                        // offsets accumulated per TMEM partial before promotion
   int tc_min_level = kTcMinLevel;          // first level on the tensor cores in the mixed forms
-  int tc_cluster = 2;                      // CTAs per cluster sharing the tensor-core A tiles (1, 2, 4)
   // learned table correction (MLP weights) and its training buffers
   float* corr_w = nullptr;                 // mlp::kParams weights (device) or unset
   int has_corr = 0;
@@ -144,6 +143,8 @@ cudaError_t setup_p2p(const Plan& P);
 // Each returns cudaGetLastError() after the launch.
 cudaError_t launch_tables(Plan& P, cudaStream_t s);
 cudaError_t launch_mean(Plan& P, const float* rho, cudaStream_t s);
+// The same reduction into caller scratch (P.n_partials partials, 1 mean).
+cudaError_t launch_mean_into(const Plan& P, const float* rho, double* partials, double* mean, cudaStream_t s);
 cudaError_t launch_p2m(Plan& P, const float* rho, cudaStream_t s);
 cudaError_t launch_m2m(Plan& P, int level, cudaStream_t s);       // level+1 -> level
 cudaError_t launch_m2l_fp32(Plan& P, int level, cudaStream_t s);  // writes F[level] (and F64[level] when coarse)
@@ -161,12 +162,14 @@ cudaError_t launch_adam(float* w, const float* g, float* m, float* v, size_t n, 
 cudaError_t launch_mesh_green(int N, float* out, int sms, cudaStream_t s);
 // Sampled error against the direct periodic sum with G_S1 (errstats.cu):
 // targets T <= error_stats_max_samples(), partials error_stats_grid_x(P, T)
-// x T x 4 doubles, sums 4 doubles.
+// x T x 4 doubles, sums 4 doubles, mean_scratch P.n_partials + 1 doubles
+// (the density mean of the statement is its own, the plan's mean stage is
+// left as the last solve wrote it).
 int error_stats_max_samples();
 int error_stats_grid_x(const Plan& P, int T);
 cudaError_t launch_error_stats(Plan& P, const float* rho, const float* phi, const float* acc,
                                const unsigned long long* targets, int T, double* partials, double* sums,
-                               cudaStream_t s);
+                               double* mean_scratch, cudaStream_t s);
 cudaError_t launch_tab_bf16(Plan& P, int level, cudaStream_t s);
 cudaError_t launch_split_bf16(Plan& P, int level, cudaStream_t s);
 cudaError_t launch_m2l_tc(Plan& P, int level, int mode, cudaStream_t s);

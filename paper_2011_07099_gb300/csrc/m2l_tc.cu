@@ -30,9 +30,11 @@
 // Layout: canonical no-swizzle K-major core matrices (8 rows x 16 B).
 // bf16x3 mode accumulates A_hi B_hi + A_hi B_lo + A_lo B_hi; bf16 mode A_hi B_hi.
 // TMEM: 512 columns = partial[0] | partial[1] | total | compensation.
-// Every wait is bounded; a timeout sets the plan's error word, later work is
-// skipped without leaving any barrier sequence, TMEM is freed and the kernel
-// returns.
+// Every wait is bounded; a timeout sets the plan's error word and later work
+// is skipped without leaving any barrier sequence.  Before the CTA exits the
+// issuer waits (bounded) for the completion of every MMA it issued and the
+// copy thread for every A copy it issued, so nothing is still in flight into
+// this CTA's TMEM or shared memory; then TMEM is freed and the kernel returns.
 #include <cuda_bf16.h>
 
 #include "fmm_internal.cuh"
@@ -71,12 +73,7 @@ constexpr int kOffSlots = 343;
 
 __device__ __forceinline__ void producer_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kProd) : "memory"); }
 
-// CL > 1: the kernel runs as clusters of CL CTAs along the target-tile axis
-// (same row tile, same child type, so the same A tiles): each CTA copies 1/CL
-// of every A stage and multicasts it to the whole cluster, and every CTA's MMA
-// completion releases the stage in all of them (their empty barriers count CL
-// arrivals), which divides the A traffic from L2 by CL.
-template <int P, int MODE, int CL>
+template <int P, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre,
          const int8_t* __restrict__ offs, int n_off, int level, int group,
@@ -92,7 +89,10 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* stages = smem;                                                // ST * STAGE_BYTES: A tiles | B tiles
   int* srckey = reinterpret_cast<int*>(smem + ST * STAGE_BYTES);         // 2 x kNT
-  __shared__ uint64_t full[ST], empty[ST], pfull[2], pfree[2];
+  // full: the producers' cp.async gathers of B landed; afull: the bulk copy of
+  // A landed (its own barrier, so that a CTA that gives up can still wait for
+  // exactly the copies it issued); empty: the MMAs reading the stage are done.
+  __shared__ uint64_t full[ST], afull[ST], empty[ST], pfull[2], pfree[2], mdone;
   __shared__ uint32_t tmem_holder;
   __shared__ int s_err;
 
@@ -103,25 +103,24 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
   const uint32_t par0 = (uint32_t)nt * kNT;
   const int8_t* my_offs = offs + (size_t)ctype * n_off * 3;
   const int n_grp = (n_off + group - 1) / group;
-  const uint32_t crank = CL > 1 ? tc::cluster_ctarank() : 0u;
-  constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
 
   if (tid == 0) {
     s_err = 0;
     for (int i = 0; i < ST; ++i) {
-      tc::mbar_init(&full[i], kProd + 1);      // kProd cp.async-completion arrivals + the A expect_tx arrival
-      tc::mbar_init(&empty[i], CL);          // one MMA completion per CTA of the cluster
+      tc::mbar_init(&full[i], kProd);          // one cp.async-completion arrival per producer thread
+      tc::mbar_init(&afull[i], 1);             // the A expect_tx arrival (+ its bytes)
+      tc::mbar_init(&empty[i], 1);             // one MMA completion
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&pfull[b], 1);
       tc::mbar_init(&pfree[b], kDrain);
     }
+    tc::mbar_init(&mdone, 1);
     tc::mbar_fence_init();
   }
   if (warp == 0) tc::tmem_alloc(&tmem_holder, kTmemCols);
   tc::fence_before_sync();
   __syncthreads();
-  if (CL > 1) tc::cluster_sync();            // every CTA's barriers exist before any multicast
   tc::fence_after_sync();
   const uint32_t tmem = tmem_holder;
   const uint32_t t_tot = tmem + 256, t_cmp = tmem + 384;
@@ -131,9 +130,9 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
     // ------------------------------------------------------------ MMA issuer
     // (`stall` is a test hook: the issuer does nothing, so every dependent
     // bounded wait of this CTA expires and the error path runs)
-    if (lane == 0 && !stall) {
+    if (lane == 0) {
       bool ok = true;
-      for (int io = 0; io < n_off && ok; ++io) {
+      for (int io = 0; io < n_off && ok && !stall; ++io) {
         const int g = io / group, b = g & 1;
         const bool first = (io % group) == 0;
         if (first && g >= 2 && !tc::mbar_wait_bounded(&pfree[b], (uint32_t)((g - 2) >> 1) & 1u, kWaitNs)) {
@@ -144,7 +143,8 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
         const uint32_t dst = tmem + (uint32_t)(b * kNT);
         for (int ch = 0; ch < NCH; ++ch) {
           const int it = io * NCH + ch, st = it % ST;
-          if (!tc::mbar_wait_bounded(&full[st], (uint32_t)(it / ST) & 1u, kWaitNs)) {
+          const uint32_t ph = (uint32_t)(it / ST) & 1u;
+          if (!tc::mbar_wait_bounded(&afull[st], ph, kWaitNs) || !tc::mbar_wait_bounded(&full[st], ph, kWaitNs)) {
             ok = false;
             break;
           }
@@ -164,20 +164,22 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
               tc::mma_bf16(dst, al, bh, IDESC, 1u);
             }
           }
-          if (CL > 1)
-            tc::mma_commit_mc(&empty[st], kMask);
-          else
-            tc::mma_commit(&empty[st]);
+          tc::mma_commit(&empty[st]);
         }
         if (ok && ((io % group) == group - 1 || io == n_off - 1)) tc::mma_commit(&pfull[b]);
       }
-      if (!ok) atomicExch(&s_err, 1);
+      // every MMA this thread issued has finished before TMEM is released,
+      // also when a wait gave up part-way
+      tc::mma_commit(&mdone);
+      if (!tc::mbar_wait_bounded(&mdone, 0u, kWaitNs)) ok = false;
+      if (!ok || stall) atomicExch(&s_err, 1);
     }
     __syncwarp();
   } else if (warp <= 4) {
     // ------------------------------------------------------------- producers
     const int pt = tid - 32;   // 0..127
     bool ok = true;            // sticky; after a timeout only the barrier sequence is kept
+    int armed = 0;             // (pt == 0) stages whose A copy was issued: iterations [0, armed)
     const int piece = pt & 7, c8 = piece >> 1, split = piece & 1;
     for (int io = 0; io < n_off; ++io) {
       const int b = io & 1;
@@ -203,16 +205,11 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
         const uint32_t sA = smem_base + st * STAGE_BYTES;
         const uint32_t sB = sA + NSPLIT * kTileBytes;
         if (pt == 0) {
-          tc::mbar_arrive_expect_tx(&full[st], A_TX);     // all of A lands here, 1/CL from each CTA
-          if (CL > 1) {
-            constexpr uint32_t chunk = A_TX / CL;
-            tc::bulk_g2s_mc(sA + crank * chunk, atile + (size_t)ch * 2 * kTileBytes + crank * chunk, chunk,
-                            &full[st], kMask);
-          } else {
-            tc::bulk_g2s(sA, atile + (size_t)ch * 2 * kTileBytes, kTileBytes, &full[st]);
-            if (MODE == 3)
-              tc::bulk_g2s(sA + kTileBytes, atile + ((size_t)ch * 2 + 1) * kTileBytes, kTileBytes, &full[st]);
-          }
+          tc::mbar_arrive_expect_tx(&afull[st], A_TX);
+          tc::bulk_g2s(sA, atile + (size_t)ch * 2 * kTileBytes, kTileBytes, &afull[st]);
+          if (MODE == 3)
+            tc::bulk_g2s(sA + kTileBytes, atile + ((size_t)ch * 2 + 1) * kTileBytes, kTileBytes, &afull[st]);
+          armed = it + 1;
         }
 #pragma unroll
         for (int pass = 0; pass < 8; ++pass) {
@@ -229,13 +226,12 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
     }
     tc::cp_async_wait<0>();
     asm volatile("cp.async.wait_all;" ::: "memory");
-    // cluster tail: the last MMA completions of every CTA arrive on this
-    // CTA's empty barriers; wait for them (bounded) so that nothing is still
-    // to arrive here when the cluster leaves
-    if (CL > 1 && ok && pt == 0) {
-      const int total = n_off * NCH;
-      for (int it = total - ST > 0 ? total - ST : 0; it < total && ok; ++it)
-        if (!tc::mbar_wait_bounded(&empty[it % ST], (uint32_t)(it / ST) & 1u, kWaitNs)) ok = false;
+    // the A copies issued last may not have been consumed (after a timeout):
+    // wait (bounded) until each has landed, so no copy is in flight into this
+    // CTA's shared memory when it exits
+    if (pt == 0) {
+      for (int it = armed - ST > 0 ? armed - ST : 0; it < armed; ++it)
+        if (!tc::mbar_wait_bounded(&afull[it % ST], (uint32_t)(it / ST) & 1u, kWaitNs)) ok = false;
     }
     if (!ok) atomicExch(&s_err, 1);
   } else {
@@ -303,7 +299,6 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (CL > 1) tc::cluster_sync();            // no CTA leaves while a peer may still signal it
   if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
   if (tid == 0 && s_err) atomicExch(err, 1);
 }
@@ -362,13 +357,7 @@ constexpr size_t smem_bytes() {
 
 template <int P, int MODE>
 cudaError_t setup_one() {
-  cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<P, MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes<P, MODE>());
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_m2l_tc<P, MODE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem_bytes<P, MODE>());
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_m2l_tc<P, MODE, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_m2l_tc<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem_bytes<P, MODE>());
 }
 
@@ -378,30 +367,7 @@ cudaError_t launch_one(Plan& Pl, int level, cudaStream_t s) {
   dim3 grid(TcShape<P, MODE>::MT, (n_par + kNT - 1) / kNT, 8);
   const __nv_bfloat16* Msp = static_cast<const __nv_bfloat16*>(Pl.Mbf_hi[level]);
   const uint8_t* Apre = static_cast<const uint8_t*>(Pl.Apre[level]);
-  const int cl = Pl.tc_cluster;
-  if (cl > 1 && grid.y % cl == 0) {
-    // clusters of CTAs along the target tiles share (multicast) their A tiles
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = smem_bytes<P, MODE>();
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 1;
-    attr[0].val.clusterDim.y = cl;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (cl == 4)
-      return cudaLaunchKernelEx(&cfg, k_m2l_tc<P, MODE, 4>, Msp, Apre, (const int8_t*)Pl.offsets[level],
-                                Pl.n_off[level], level, Pl.tc_group, Pl.F[level], Pl.d_err, Pl.wait_ns,
-                                Pl.inject_stall);
-    return cudaLaunchKernelEx(&cfg, k_m2l_tc<P, MODE, 2>, Msp, Apre, (const int8_t*)Pl.offsets[level],
-                              Pl.n_off[level], level, Pl.tc_group, Pl.F[level], Pl.d_err, Pl.wait_ns,
-                              Pl.inject_stall);
-  }
-  k_m2l_tc<P, MODE, 1><<<grid, kThreads, smem_bytes<P, MODE>(), s>>>(
+  k_m2l_tc<P, MODE><<<grid, kThreads, smem_bytes<P, MODE>(), s>>>(
       Msp, Apre, Pl.offsets[level], Pl.n_off[level], level, Pl.tc_group, Pl.F[level], Pl.d_err, Pl.wait_ns,
       Pl.inject_stall);
   return cudaGetLastError();

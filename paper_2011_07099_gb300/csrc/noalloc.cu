@@ -9,6 +9,8 @@
 // process exits, so the call itself allocates nothing.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "fmm_internal.cuh"
 
 namespace {
@@ -23,8 +25,10 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_partials[kMaxBlocks];
 
 // Device address of g_partials per device, looked up on the first call made
-// with that device current.
-double* g_partials_addr[kMaxDevices] = {};
+// with that device current.  Atomic slots: host threads that make their first
+// call on the same device at the same time may both look the address up, and
+// both store the same value, without a data race.
+std::atomic<double*> g_partials_addr[kMaxDevices] = {};
 
 __global__ void k_block_sums(const float* __restrict__ rho, size_t count, double* __restrict__ partials) {
   const size_t begin = (size_t)blockIdx.x * kCellsPerBlock;
@@ -69,14 +73,13 @@ extern "C" int fmm_mean_density_noalloc(const float* density, size_t count, doub
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return set_last_error(FMM_ERR_CUDA);
   if (dev < 0 || dev >= kMaxDevices) return set_last_error(FMM_ERR_UNSUPPORTED);
-  if (!g_partials_addr[dev]) {
+  double* partials = g_partials_addr[dev].load(std::memory_order_acquire);
+  if (!partials) {
     // one-time set-up for this device: the static array's device address
-    double* ptr = nullptr;
-    if (cudaGetSymbolAddress(reinterpret_cast<void**>(&ptr), g_partials) != cudaSuccess || !ptr)
+    if (cudaGetSymbolAddress(reinterpret_cast<void**>(&partials), g_partials) != cudaSuccess || !partials)
       return set_last_error(FMM_ERR_CUDA);
-    g_partials_addr[dev] = ptr;
+    g_partials_addr[dev].store(partials, std::memory_order_release);
   }
-  double* partials = g_partials_addr[dev];
   const int blocks = (int)((count + kCellsPerBlock - 1) / kCellsPerBlock);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   k_block_sums<<<blocks, 256, 0, s>>>(density, count, partials);

@@ -1,8 +1,8 @@
 // Inline-PTX helpers for the 5th-generation tensor cores (tcgen05) of sm_103a:
 // TMEM allocation, shared-memory matrix descriptors, the instruction
-// descriptor of kind::f16, MMA issue/commit (also multicast to a cluster),
-// bounded mbarrier waits, TMEM loads/stores, bulk and cp.async copies and
-// cluster barriers.  Written from the public PTX ISA descriptions.
+// descriptor of kind::f16, MMA issue/commit, bounded mbarrier waits, TMEM
+// loads/stores, bulk and cp.async copies.  Written from the public PTX ISA
+// descriptions.
 #pragma once
 
 #include <cstdint>
@@ -148,37 +148,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(smem_u32(mbar))
                : "memory");
-}
-
-// ---------------------------------------------------------------- clusters
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-// All threads of every CTA of the cluster arrive (release) and wait (acquire).
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
-  asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
-}
-// 1-D bulk copy global -> shared of every CTA in `mask` (same shared-memory
-// offset in each); each destination CTA's mbarrier at the offset of `mbar`
-// receives the byte count.
-__device__ __forceinline__ void bulk_g2s_mc(uint32_t dst, const void* src, uint32_t bytes, uint64_t* mbar,
-                                            uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;" ::"r"(
-          dst),
-      "l"(src), "r"(bytes), "r"(smem_u32(mbar)), "h"(mask)
-      : "memory");
-}
-// As mma_commit, arriving on the mbarrier at the same offset in every CTA of `mask`.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* mbar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(mbar)),
-      "h"(mask)
-      : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {

@@ -128,11 +128,15 @@ cudaError_t setup_upward(const Plan& P) {
   return cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-cudaError_t launch_mean(Plan& P, const float* rho, cudaStream_t s) {
+cudaError_t launch_mean_into(const Plan& P, const float* rho, double* partials, double* mean, cudaStream_t s) {
   const size_t n4 = (size_t)P.N * P.N * P.N / 4;
-  k_partial_sum<<<P.n_partials, 256, 0, s>>>(reinterpret_cast<const float4*>(rho), n4, P.d_partials);
-  k_final_mean<<<1, 1024, 0, s>>>(P.d_partials, P.n_partials, 1.0 / ((double)P.N * P.N * P.N), P.d_mean);
+  k_partial_sum<<<P.n_partials, 256, 0, s>>>(reinterpret_cast<const float4*>(rho), n4, partials);
+  k_final_mean<<<1, 1024, 0, s>>>(partials, P.n_partials, 1.0 / ((double)P.N * P.N * P.N), mean);
   return cudaGetLastError();
+}
+
+cudaError_t launch_mean(Plan& P, const float* rho, cudaStream_t s) {
+  return launch_mean_into(P, rho, P.d_partials, P.d_mean, s);
 }
 
 cudaError_t launch_p2m(Plan& P, const float* rho, cudaStream_t s) {

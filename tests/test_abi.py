@@ -69,8 +69,8 @@ def test_null_plan_calls_fail_cleanly(lib):
 def test_setters_validate_before_touching_the_device(lib):
     # null plans and out-of-range knobs are refused on the host
     L = binding.lib()
-    for call in (lambda: L.fmm_plan_set_m2l_group(None, 2), lambda: L.fmm_plan_set_m2l_cluster(None, 2),
-                 lambda: L.fmm_plan_set_tc_min_level(None, 4), lambda: L.fmm_plan_set_timeout_ms(None, 100),
+    for call in (lambda: L.fmm_plan_set_m2l_group(None, 2), lambda: L.fmm_plan_set_tc_min_level(None, 4),
+                 lambda: L.fmm_plan_set_timeout_ms(None, 100),
                  lambda: L.fmm_plan_inject_fault(None, 0), lambda: L.fmm_plan_set_correction_inference(None, 0),
                  lambda: L.fmm_plan_error_stats(None, None, None, None, 16, 0, None, None)):
         assert call() == binding.FMM_ERR_ARG

@@ -73,28 +73,6 @@ def test_bf16x3_promotion_group_sizes(B, group):
     assert _rel(acc, og) <= tol
 
 
-@pytest.mark.parametrize("ctas", [1, 2, 4])
-def test_cluster_multicast_gives_identical_results(B, ctas):
-    # clusters only change where the translation tiles come from: results are
-    # bitwise the same for every cluster size
-    N, L, p = 64, 4, 4
-    rho = inputs.plummer(N, n_clumps=16, seed=6)
-    d = torch.from_numpy(rho).cuda()
-    outs = []
-    for c in (1, ctas):
-        plan = B.Plan(N, L, p)
-        plan.set_precision(B.FMM_PREC_BF16X3)
-        B.fmm_plan_set_m2l_cluster(plan.handle, c)
-        phi, acc = plan.solve(d)
-        torch.cuda.synchronize()
-        assert B.lib().fmm_plan_check(plan.handle) == B.FMM_OK
-        outs.append((phi.clone(), acc.clone()))
-        plan.close()
-    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
-    ophi, og = ofmm.solve(rho, L, p)
-    assert _rel(outs[1][0].cpu().numpy(), ophi) <= TOL_BF16X3
-
-
 def test_bf16_matches_oracle(B):
     N, L, p = 64, 4, 4
     rho = inputs.lognormal(N, sigma=0.5, seed=1)
@@ -139,22 +117,27 @@ def test_mixed_form_within_1e4_of_pm_at_256(B):
     assert e_phi <= 1e-4 and e_g <= 1e-4
 
 
-def test_bounded_wait_expires_and_context_survives(B):
+@pytest.mark.parametrize("limit_ms", [100, 1])
+def test_bounded_wait_expires_and_context_survives(B, limit_ms):
     # a stalled MMA issuer (test hook) makes every dependent wait run out: the
-    # kernel returns, the error word reads FMM_ERR_TIMEOUT, and the next solve
-    # on the same context is correct
+    # kernel drains what it issued and returns, the error word reads
+    # FMM_ERR_TIMEOUT, and the next solve on the same context is correct (with
+    # the default limit restored)
     N, L, p = 32, 4, 2
     rho = inputs.lognormal(N, sigma=0.5, seed=2)
     plan = B.Plan(N, L, p)
     plan.set_precision(B.FMM_PREC_BF16X3)
-    B.fmm_plan_set_timeout_ms(plan.handle, 100)
+    B.fmm_plan_set_timeout_ms(plan.handle, limit_ms)
     B.fmm_plan_inject_fault(plan.handle, B.FMM_FAULT_TC_STALL)
     d = torch.from_numpy(rho).cuda()
     plan.solve(d)
     assert B.lib().fmm_plan_check(plan.handle) == B.FMM_ERR_TIMEOUT
     B.fmm_plan_inject_fault(plan.handle, B.FMM_FAULT_NONE)
-    phi, acc = plan.solve(d)
-    assert B.lib().fmm_plan_check(plan.handle) == B.FMM_OK
+    B.fmm_plan_set_timeout_ms(plan.handle, 2000)
     ophi, og = ofmm.solve(rho, L, p)
-    assert _rel(phi.cpu().numpy(), ophi) <= TOL_BF16X3
+    for _ in range(2):
+        phi, acc = plan.solve(d)
+        assert B.lib().fmm_plan_check(plan.handle) == B.FMM_OK
+        assert _rel(phi.cpu().numpy(), ophi) <= TOL_BF16X3
+        assert _rel(acc.cpu().numpy(), og) <= TOL_BF16X3
     plan.close()

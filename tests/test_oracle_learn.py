@@ -2,8 +2,9 @@
 from math import erf, sqrt
 
 import numpy as np
+import pytest
 
-from oracle import fmm, learn
+from oracle import fmm, green, learn, pm
 from paper_2011_07099_gb300 import inputs
 
 
@@ -66,3 +67,60 @@ def test_zero_weights_give_the_plain_fmm():
     a = fmm.solve(rho, 3, 2)
     b = fmm.solve(rho, 3, 2, correction=learn.correction_fn(np.zeros(learn.N_PARAMS)))
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def _brute_corrected(rho, w, S):
+    """Direct periodic sum of the two-level tree (L = 2, p = S) with the
+    corrected kernel written out per cell pair: at level 2 the gridlet points
+    are the cell centres (spacing 1/N), so the interaction-zone pairs use
+    G_S1 plus the table correction at n = target cell - source cell (x, y, z),
+    and the 27 neighbour leaves use G_S1 alone (the near zone is exact)."""
+    N = rho.shape[0]
+    m = pm.masses(np.asarray(rho, np.float64)).ravel()
+    idx = np.indices((N, N, N)).reshape(3, -1).T                  # (z, y, x), row-major cell order
+    xyz = idx[:, ::-1]
+    d = xyz[:, None, :] - xyz[None, :, :]                          # (target, source, 3) in cells
+    leaf = idx // S
+    near = np.all(np.isin((leaf[:, None, :] - leaf[None, :, :]) % 4, [0, 1, 3]), axis=-1)
+    G = green.g_s1(d / N, self_value=green.self_term(N))
+    mdG = -green.grad_g_s1(d / N)                                  # (t, s, 3)
+    uniq, inv = np.unique(d.reshape(-1, 3), axis=0, return_inverse=True)
+    corr = learn.table_correction(w, 2, S, uniq)[inv.ravel()].reshape(N ** 3, N ** 3, 4)
+    corr[near] = 0.0
+    phi = (G + corr[..., 0]) @ m
+    g = np.stack([(mdG[..., c] + corr[..., 1 + c]) @ m for c in range(3)])
+    return phi.reshape(N, N, N), g.reshape(3, N, N, N)
+
+
+@pytest.mark.parametrize("N", [8, 12])
+def test_corrected_two_level_tree_equals_the_corrected_direct_sum(N):
+    # Sec. 3's exact case (two levels, gridlet = sub-grid) carried over to the
+    # corrected tables: the FMM with correction_fn(w) must equal the direct
+    # sum whose far-zone kernel is G_S1 + table_correction at the cell offset.
+    # This pins the mapping n = o p + r - s of the correction into eq. fmm2.
+    S = N // 4
+    rho = inputs.plummer(N, n_clumps=3, seed=N, a_min=0.5, a_max=2.0)
+    w = np.random.default_rng(N).normal(0.0, 0.5, learn.N_PARAMS)
+    phi, g = fmm.solve(rho, 2, S, correction=learn.correction_fn(w))
+    bphi, bg = _brute_corrected(rho, w, S)
+    plain_phi, plain_g = fmm.solve(rho, 2, S)
+    # the correction is not negligible at this weight scale ...
+    assert np.linalg.norm(plain_phi - bphi) / np.linalg.norm(bphi) > 1e-5
+    assert np.linalg.norm(plain_g - bg) / np.linalg.norm(bg) > 1e-5
+    # ... and the corrected FMM reproduces the corrected direct sum exactly
+    assert np.linalg.norm(phi - bphi) / np.linalg.norm(bphi) < 1e-12
+    assert np.linalg.norm(g - bg) / np.linalg.norm(bg) < 1e-12
+
+
+def test_planted_flip_of_r_minus_s_in_the_correction_is_caught():
+    # n = o p + s - r instead of o p + r - s: the translation matrices of the
+    # correction come out transposed in (r, s), and the exact case fails
+    N, S = 8, 2
+    rho = inputs.plummer(N, n_clumps=3, seed=N, a_min=0.5, a_max=2.0)
+    w = np.random.default_rng(N).normal(0.0, 0.5, learn.N_PARAMS)
+    good = learn.correction_fn(w)
+    flipped = lambda level, p, off: np.swapaxes(good(level, p, off), 1, 2)
+    phi, g = fmm.solve(rho, 2, S, correction=flipped)
+    bphi, bg = _brute_corrected(rho, w, S)
+    assert np.linalg.norm(phi - bphi) / np.linalg.norm(bphi) > 1e-5
+    assert np.linalg.norm(g - bg) / np.linalg.norm(bg) > 1e-3
