@@ -39,8 +39,7 @@ DEFAULT_CORRECTION = os.path.join(os.path.dirname(os.path.abspath(__file__)), "p
                                   "correction_p6.npz")
 UNIT = "cells/s"
 FP32_FMA_PER_SM_PER_CLK = 128        # FP32 lanes per SM (4 partitions x 32)
-SM_COUNT = 152
-SM_MAX_MHZ = 2070.0
+SM_MAX_MHZ = 2070.0                  # used only when neither nvidia-smi nor MEASURED_PEAKS.json gives it
 
 
 def _peaks():
@@ -139,9 +138,44 @@ def workload_density(n, field):
     return inputs.lognormal(n, sigma=0.5, seed=5000 + field)
 
 
-# DRAM bytes (read + write) of one k_p2p launch from the ncu capture of the
-# current kernel in profiles/k_p2p_256cube_p6.md
+# DRAM bytes (read + write) of one k_p2p launch, from an ncu capture of the
+# current kernel at 256^3, p = 6, L = 5 (dram__bytes_read.sum +
+# dram__bytes_write.sum); not measured in this run
 P2P_TRAFFIC = {(256, 5, 6): 419.8e6}
+P2P_TRAFFIC_SOURCE = "ncu capture of the current k_p2p at 256^3 p=6 (dram__bytes read+write), not measured in this run"
+
+
+def measure_fp32_peak(B, dev, stream, reps=40):
+    """The FP32 CUDA-core peak of this device, measured: the library's FMA
+    probe (dependent FMA chains only, 2 CTAs of 1024 threads per SM), each
+    launch timed with CUDA events on the launching stream, median of `reps`
+    launches after 3 warm-ups; SM clocks are sampled meanwhile."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, iters = 2 * sms, 20000
+    out = torch.empty(blocks, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        flops = B.fmm_probe_fma(out, blocks, iters, stream)
+    torch.cuda.synchronize(dev)
+    ms = []
+    with ClockSampler(dev.index) as clk:
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.fmm_probe_fma(out, blocks, iters, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    med = statistics.median(ms)
+    c = clk.summary() or {}
+    max_mhz = c.get("sm_max_mhz") or SM_MAX_MHZ
+    derived = sms * FP32_FMA_PER_SM_PER_CLK * 2 * max_mhz * 1e6 / 1e12
+    return {"tflops": flops / (med / 1e3) / 1e12, "launch_ms": med, "sm_count": sms,
+            "sm_mhz_median": c.get("sm_mhz"), "sm_max_mhz": max_mhz, "clock_reasons": c.get("reasons"),
+            "derived_at_max_clock_tflops": derived,
+            "how": f"fmm_probe_fma: {blocks} CTAs x 1024 threads x 8 FMA chains x {iters} x 16, CUDA events, "
+                   f"median of {reps}"}
 
 
 def p2p_flops(N, L):
@@ -179,16 +213,21 @@ def effective_cores(cpu_seconds, wall_seconds):
     return round(cpu_seconds / wall_seconds, 1) if wall_seconds > 0 else 0.0
 
 
-def accuracy_vs_pm(rho, phi, acc):
-    """Part of the oracle leg: relative L2 of the timed solve's result against
-    PM with the same Green's function (FFT convolution, FP64 host) and,
-    secondary, against the spectral PM with G_K."""
+def pm_references(rho):
+    """Part of the oracle leg: PM with the same Green's function (FFT
+    convolution, FP64 host) and, secondary, the spectral PM with G_K."""
     import numpy as np
     from oracle import green, pm
     n = rho.shape[0]
     m = pm.masses(rho.astype(np.float64))
-    pphi, pg = pm.pm(m, green.g_s1, green.grad_g_s1, green.self_term(n))
-    kphi, kg = pm.pm_gk(m)
+    return pm.pm(m, green.g_s1, green.grad_g_s1, green.self_term(n)), pm.pm_gk(m)
+
+
+def accuracy_vs_pm(refs, phi, acc):
+    """Relative L2 over all cells of a result against PM(G_S1) (primary: the
+    same G in PM and FMM) and PM(G_K) (secondary)."""
+    import numpy as np
+    (pphi, pg), (kphi, kg) = refs
     rel = lambda a, b: float(np.linalg.norm(a.astype(np.float64) - b) / np.linalg.norm(b))
     return {"vs_pm_gs1": {"phi": rel(phi, pphi), "g": rel(acc, pg)},
             "vs_pm_gk": {"phi": rel(phi - phi.mean(), kphi - kphi.mean()), "g": rel(acc, kg)},
@@ -224,8 +263,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     from oracle import fmm as ofmm
-    n, L, p = 32, 2, 6
-    rho = workload_density(n, 0)
+    n, L, p = 64, 3, 6            # the cpu_baseline sample: levels 2 and 3, M2M and L2L, S = 8
+    rho = workload_density(64, 0)
     for _ in range(args.warmup):
         ofmm.solve(rho, L, p)
     times = []
@@ -240,7 +279,9 @@ def run_reference(args):
     sample = (f"FP64 numpy oracle (plain method, no correction), full solve of a {n}^3 lognormal sigma=0.5 "
               f"field per step with order p={p} and the workload's leaf size S=8 (L={L}); cells/s of the "
               f"sample stand for the {args.n}^3 workload")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+    line = {"impl": "reference", "method": "the plain method in FP64 (CPU oracle): no tensor cores, no "
+                                          "mixed precision, no learned correction",
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": headline_config(args, learned_correction(args), ws),
@@ -280,8 +321,14 @@ def _time_solves(B, plan, rho, phi, acc, steps, warmup, l2_flush, stream, barrie
     barrier()
     wall = time.perf_counter() - wall0
     B.fmm_plan_set_timing(plan.handle, False)
-    B.fmm_plan_check(plan.handle)
     return step_ms, stage, wall
+
+
+def device_check(B, plan):
+    """fmm_plan_check after a loop of solves: "ok", or the error it reports
+    (a bounded device wait that ran out makes those results invalid)."""
+    rc = B.lib().fmm_plan_check(plan.handle)
+    return "ok" if rc == B.FMM_OK else B.lib().fmm_error_string(rc).decode()
 
 
 def launches_per_solve(L, tc, p=6):
@@ -295,10 +342,10 @@ def launches_per_solve(L, tc, p=6):
     return 2 + 1 + (L - 2) + m2l + (L - 2) + 1
 
 
-def solve_roofline(n, L, p, tc, ms, peaks):
+def solve_roofline(n, L, p, tc, ms, peaks, fp32_tflops):
     """Ideal time of the whole solve (each step at its own bound: FP32 FMA,
     BF16 tensor (executed products), HBM bytes) against the measured step."""
-    fp32 = 152 * 128 * 2 * 2.07e9
+    fp32 = fp32_tflops * 1e12
     bf16 = peaks.get("bf16_tflops_sustained", 1700.0) * 1e12
     hbm = peaks.get("hbm_gbs", 6500.0) * 1e9
     p3 = p ** 3
@@ -317,7 +364,8 @@ def solve_roofline(n, L, p, tc, ms, peaks):
     ideal = sum(t.values()) * 1e3
     return {"ideal_ms": ideal, "measured_ms": ms, "frac": ideal / ms,
             "terms_ms": {k: v * 1e3 for k, v in t.items()},
-            "peaks": "FP32 80.5 TFLOP/s (derived), BF16 sustained and HBM from MEASURED_PEAKS.json"}
+            "peaks": f"FP32 {fp32_tflops:.1f} TFLOP/s (measured, fmm_probe_fma), BF16 sustained and HBM from "
+                     "MEASURED_PEAKS.json"}
 
 
 def run_ours(args):
@@ -361,19 +409,46 @@ def run_ours(args):
     with ClockSampler(dev.index) as clk:
         step_ms, stage, wall = _time_solves(B, plan, rho, phi, acc, args.steps, args.warmup, l2_flush, stream,
                                             barrier)
+    checks = {"timed_solves": device_check(B, plan)}
     ms = slowest_rank_ms(statistics.mean(step_ms), ws, dev)
     value = whole_job_cells_per_s(ws, n, ms)
-    result_phi = phi.cpu().numpy() if (rank == 0 and ws == 1 and not args.no_cpu_baseline) else None
-    result_acc = acc.cpu().numpy() if result_phi is not None else None
+    host_leg = rank == 0 and ws == 1 and not args.no_cpu_baseline
+    result_phi = phi.cpu().numpy() if host_leg else None
+    result_acc = acc.cpu().numpy() if host_leg else None
     # the library's own statement of this result's error against PM with
     # G_S1, measured exactly at sampled cells (outside the timed region)
     stmt_cells = 256
-    try:
-        e_phi, e_g = plan.error_stats(rho, phi, acc, samples=stmt_cells, seed=1)
-        statement = {"vs_pm_gs1": {"phi": e_phi, "g": e_g}, "cells": stmt_cells,
-                     "source": "fmm_plan_error_stats (exact direct sum at sampled cells, GPU)"}
-    except B.FMMError as e:   # reported in the line; the timed numbers stand
-        statement = {"failed": str(e)}
+
+    def statement_of(pl, ph, ac):
+        try:
+            e_phi, e_g = pl.error_stats(rho, ph, ac, samples=stmt_cells, seed=1)
+            return {"vs_pm_gs1": {"phi": e_phi, "g": e_g}, "cells": stmt_cells,
+                    "source": "fmm_plan_error_stats (exact direct sum at sampled cells, GPU)"}
+        except B.FMMError as e:   # reported in the line; the timed numbers stand
+            return {"failed": str(e)}
+
+    statement = statement_of(plan, phi, acc)
+    checks["error_statement"] = device_check(B, plan)
+
+    # what the learned correction gains on the timed field: the same form
+    # without the correction, solved once (outside the timed region)
+    gain = None
+    if learned is not None:
+        nplan = B.Plan(n, L, p)
+        if tc:
+            nplan.set_precision(prec)
+        nphi = torch.empty_like(phi)
+        nacc = torch.empty_like(acc)
+        nplan.solve(rho, nphi, nacc)
+        torch.cuda.synchronize(dev)
+        checks["without_correction"] = device_check(B, nplan)
+        gain = {"with_correction": statement.get("vs_pm_gs1"),
+                "without_correction": statement_of(nplan, nphi, nacc).get("vs_pm_gs1"),
+                "measured_by": f"fmm_plan_error_stats, {stmt_cells} cells (seed 1), same cells for both"}
+        if host_leg:
+            gain["without_correction_host_pm"] = ("pending", nphi.cpu().numpy(), nacc.cpu().numpy())
+        nplan.close()
+        del nphi, nacc
 
     # per-stage means over the timed steps
     nslot = len(stage[0])
@@ -389,6 +464,7 @@ def run_ours(args):
         pplan = B.Plan(n, L, p)
         pms, pstage, _ = _time_solves(B, pplan, rho, phi, acc, max(1, min(args.steps, 3)), max(1, min(args.warmup, 2)),
                                       l2_flush, stream, barrier)
+        checks["plain_fp32"] = device_check(B, pplan)
         pm_ = slowest_rank_ms(statistics.mean(pms), ws, dev)
         plain = {"value": whole_job_cells_per_s(ws, n, pm_), "ms_per_step": pm_,
                  "m2l_ms": statistics.mean(s[B.FMM_TIME_M2L] for s in pstage),
@@ -396,13 +472,15 @@ def run_ours(args):
         pplan.close()
 
     peaks, src = _peaks()
-    fp32_peak = SM_COUNT * FP32_FMA_PER_SM_PER_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fma = measure_fp32_peak(B, dev, stream)
+    fp32_peak = fma["tflops"]
     dominant = max(names, key=lambda k: stage_ms[k])
     p2p_ach = p2p_flops(n, L) / (stage_ms["p2p_l2p"] / 1000.0) / 1e12
+    traffic = P2P_TRAFFIC.get((n, L, p))
     roof_p2p = {"kernel": "k_p2p (fused L2P + near-zone sum)", "bound": "alu", "achieved": p2p_ach,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": p2p_ach / fp32_peak,
-                "traffic": P2P_TRAFFIC.get((n, L, p)),
-                "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz (derived)"}
+                "traffic": traffic, "traffic_source": P2P_TRAFFIC_SOURCE if traffic else None,
+                "peak_source": "measured (of measured): " + fma["how"], "fp32_probe": fma}
     tc_levels = [lev for lev in range(4, L + 1)] if tc else []
     roof_m2l = None
     if tc_levels:
@@ -427,6 +505,7 @@ def run_ours(args):
     for _ in range(e2e_steps):
         B.fmm_solve_host(plan.handle, hin, hphi, hacc, stream)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    checks["e2e"] = device_check(B, plan)
     plan.close()
 
     if rank != 0:
@@ -449,16 +528,24 @@ def run_ours(args):
         "e2e": {"value": ws * n ** 3 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * n ** 3,
                 "d2h_bytes_per_step": 16 * n ** 3},
         "gpu_launches": launches_per_solve(L, tc, p) * args.steps,
-        "solve_roofline": solve_roofline(n, L, p, tc, ms, peaks),
+        "solve_roofline": solve_roofline(n, L, p, tc, ms, peaks, fp32_peak),
         "clocks": clocks,
         "error_statement": statement,
+        "device_checks": checks,
     }
     if plain is not None:
         line["plain_fp32"] = plain
         line["speedup_vs_plain_fp32"] = plain["ms_per_step"] / ms
-    if ws == 1 and not args.no_cpu_baseline:
+    if host_leg:
         line["cpu_baseline"] = cpu_baseline()
-        line["accuracy"] = accuracy_vs_pm(rho_host, result_phi, result_acc)
+        refs = pm_references(rho_host)
+        line["accuracy"] = accuracy_vs_pm(refs, result_phi, result_acc)
+        if gain is not None:
+            _, gphi, gacc = gain.pop("without_correction_host_pm")
+            gain["whole_mesh"] = {"with_correction": line["accuracy"],
+                                  "without_correction": accuracy_vs_pm(refs, gphi, gacc)}
+    if gain is not None:
+        line["learned_gain"] = gain
     print(json.dumps(line), flush=True)
     return 0
 
@@ -545,7 +632,7 @@ def run_full512(args):
             st = [statistics.mean(s_[i] for s_ in stage) for i in range(len(stage[0]))]
             out[name] = {"ms_per_step": statistics.mean(ms), "cells_per_s": n ** 3 / (statistics.mean(ms) / 1e3),
                          "m2l_ms": st[B.FMM_TIME_M2L], "p2p_ms": st[B.FMM_TIME_P2P],
-                         "vs_pm_gs1": {"phi": e_phi, "g": e_g}}
+                         "vs_pm_gs1": {"phi": e_phi, "g": e_g}, "device_check": device_check(B, plan)}
             plan.close()
             del phi, acc
     line = {"metric": "FMM cells/s at 512^3 p=8 (full scale)", "value": out["mixed_bf16x3"]["cells_per_s"],

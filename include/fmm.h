@@ -316,6 +316,19 @@ int fmm_plan_error_stats(fmm_plan* plan, const float* density, const float* pote
                          const float* accel, int samples, unsigned long long seed,
                          double* out, void* stream);
 
+/* ---- measurement aid ----------------------------------------------------- */
+
+/* FP32 FMA throughput probe; the paper has no counterpart.  Enqueues on
+ * `stream` one kernel of `blocks` CTAs x 1024 threads, each thread running 8
+ * independent chains of iters x 16 dependent FMAs, and stores one float per
+ * CTA to `out` (device, `blocks` floats).  fmm_probe_fma_flops(blocks, iters)
+ * returns the flops one launch performs (2 per FMA), so a caller that times
+ * the launch with CUDA events measures the FP32 CUDA-core peak against which
+ * the near-zone sum (an FMA-bound step) is judged.  FMM_ERR_ARG for a NULL
+ * pointer or counts < 1. */
+int fmm_probe_fma(float* out, int blocks, int iters, void* stream);
+double fmm_probe_fma_flops(int blocks, int iters);
+
 /* ---- allocation-free entry point ----------------------------------------- */
 
 /* Mean of a device float array, without any allocation by the library.  The

@@ -348,11 +348,11 @@ def solve(rho, L, p, correction=None):
     return mesh[0], mesh[1:]
 
 
-def solve_at(rho, L, p, leaves):
+def solve_at(rho, L, p, leaves, correction=None):
     """The same solve evaluated only in the given leaves ((k,3), (z,y,x)):
     the whole upward pass, then the local fields along each leaf's chain of
     ancestors, L2P and P2P in those leaves.  Returns (k, 4, S^3) with cells
-    flattened x fastest within the leaf."""
+    flattened x fastest within the leaf.  ``correction`` as in ``m2l``."""
     rho = np.asarray(rho, dtype=np.float64)
     N = rho.shape[0]
     S = N // 2 ** L
@@ -362,7 +362,7 @@ def solve_at(rho, L, p, leaves):
     loc = None
     for lev in range(2, L + 1):
         anc = leaves >> (L - lev)
-        F = m2l(lev, p, M[lev], anc)
+        F = m2l(lev, p, M[lev], anc, correction)
         if loc is not None:
             c = anc % 2
             for i in range(anc.shape[0]):

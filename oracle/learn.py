@@ -25,9 +25,10 @@ corrected table keeps the parity of each field and is periodic; the loss
 gradient of ``loss`` against central finite differences is what the GPU
 gradient is checked against.
 """
-from math import erf, sqrt
+from math import sqrt
 
 import numpy as np
+from scipy.special import erf as _erf
 
 from . import fmm, green, pm
 
@@ -49,12 +50,10 @@ def unpack(w):
     return out
 
 
-_erf = np.vectorize(erf)
-
-
 def gelu(z):
-    """z * Phi(z), Phi the standard normal CDF (erf form)."""
-    return 0.5 * z * (1.0 + _erf(z / sqrt(2.0)))
+    """z * Phi(z), Phi the standard normal CDF (erf form; the library erf
+    evaluated element-wise)."""
+    return 0.5 * z * (1.0 + _erf(np.asarray(z, dtype=np.float64) / sqrt(2.0)))
 
 
 def mlp(w, x):
@@ -109,24 +108,28 @@ def table_correction(w, level, p, n):
 def correction_fn(w):
     """The per-offset (4, p^3, p^3) correction of eq. fmm2's translation
     matrices for ``fmm.solve(..., correction=...)``: entry [f, r, s] is the
-    table correction at n = o p + r - s (x, y, z components)."""
-    cache = {}
+    table correction at n = o p + r - s (x, y, z components).  Every offset
+    of the interaction zones has |o_i| <= 3, so every such n lies in the cube
+    |n_i| <= 4p - 1: the correction is evaluated once per (level, p) on that
+    cube and looked up."""
+    tables = {}
 
     def corr(level, p, off_zyx):
-        key = (level, p, tuple(off_zyx))
-        if key in cache:
-            return cache[key]
+        h = 4 * p - 1
+        if (level, p) not in tables:
+            g = np.arange(-h, h + 1)
+            nz, ny, nx = np.meshgrid(g, g, g, indexing="ij")
+            cube = np.stack([nx.ravel(), ny.ravel(), nz.ravel()], axis=-1)     # x fastest
+            tables[(level, p)] = table_correction(w, level, p, cube).reshape(2 * h + 1, 2 * h + 1, 2 * h + 1, 4)
+        tab = tables[(level, p)]
         g = np.arange(p)
         z, y, x = np.meshgrid(g, g, g, indexing="ij")
         pts = np.stack([x.ravel(), y.ravel(), z.ravel()], axis=-1)            # (p^3, 3) x, y, z
         o = np.array(off_zyx[::-1], dtype=np.int64) * p
         nvec = o[None, None, :] + pts[:, None, :] - pts[None, :, :]           # (r, s, 3)
-        flat = nvec.reshape(-1, 3)
-        uniq, inv = np.unique(flat, axis=0, return_inverse=True)
-        c = table_correction(w, level, p, uniq)[inv.ravel()]                  # (p^6, 4)
-        K = np.moveaxis(c.reshape(p ** 3, p ** 3, 4), -1, 0)
-        cache[key] = K
-        return K
+        assert np.abs(nvec).max() <= h
+        c = tab[nvec[..., 2] + h, nvec[..., 1] + h, nvec[..., 0] + h]           # (r, s, 4)
+        return np.moveaxis(c, -1, 0)
 
     return corr
 

@@ -55,6 +55,8 @@ SIGNATURES = {
     "fmm_plan_set_timeout_ms": (_I, [_VP, _I]),
     "fmm_plan_inject_fault": (_I, [_VP, _I]),
     "fmm_mean_density_noalloc": (_I, [_FP, _SZ, _FP, _VP]),
+    "fmm_probe_fma": (_I, [_FP, _I, _I, _VP]),
+    "fmm_probe_fma_flops": (ctypes.c_double, [_I, _I]),
     "fmm_plan_set_correction": (_I, [_VP, _FP, _SZ]),
     "fmm_plan_set_correction_inference": (_I, [_VP, _I]),
     "fmm_correction_grad": (_I, [_VP, _FP, _FP, _FP, ctypes.c_float, ctypes.c_float, _FP, _FP, _VP]),
@@ -202,6 +204,11 @@ def fmm_adam_step(weights, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-
 
 def fmm_mesh_green(N, out, stream=None):
     _check(lib().fmm_mesh_green(int(N), out.data_ptr(), _stream_of(out, stream)), "fmm_mesh_green")
+
+
+def fmm_probe_fma(out, blocks, iters, stream=None):
+    _check(lib().fmm_probe_fma(out.data_ptr(), int(blocks), int(iters), _stream_of(out, stream)), "fmm_probe_fma")
+    return float(lib().fmm_probe_fma_flops(int(blocks), int(iters)))
 
 
 def fmm_plan_check(plan):

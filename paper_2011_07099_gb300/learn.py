@@ -23,6 +23,19 @@ from . import binding as B
 from . import inputs
 
 
+DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+
+
+def shipped_weights(p):
+    """The trained correction weights shipped with the package for order p
+    (float32 array of FMM_MLP_PARAMS values), or None if there are none."""
+    path = os.path.join(DATA, f"correction_p{p}.npz")
+    if not os.path.exists(path):
+        return None
+    with np.load(path) as z:
+        return np.asarray(z["w"], dtype=np.float32)
+
+
 def pm_target(density, N):
     """PM with G_S1 on the GPU: circular convolution of the mean-free masses
     with libfmm's mesh Green's function (FP64 FFTs).  Returns (phi, acc)."""

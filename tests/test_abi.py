@@ -72,7 +72,8 @@ def test_setters_validate_before_touching_the_device(lib):
     for call in (lambda: L.fmm_plan_set_m2l_group(None, 2), lambda: L.fmm_plan_set_tc_min_level(None, 4),
                  lambda: L.fmm_plan_set_timeout_ms(None, 100),
                  lambda: L.fmm_plan_inject_fault(None, 0), lambda: L.fmm_plan_set_correction_inference(None, 0),
-                 lambda: L.fmm_plan_error_stats(None, None, None, None, 16, 0, None, None)):
+                 lambda: L.fmm_plan_error_stats(None, None, None, None, 16, 0, None, None),
+                 lambda: L.fmm_probe_fma(None, 1, 1, None)):
         assert call() == binding.FMM_ERR_ARG
         assert L.fmm_last_error() == binding.FMM_ERR_ARG
 
@@ -96,3 +97,8 @@ def test_batch_and_autotuner_validate_before_touching_the_device(lib):
     assert L.fmm_autotune_levels(64, 0, 0, None, ctypes.byref(out_L), ctypes.byref(out_ms)) == binding.FMM_ERR_ARG
     assert L.fmm_autotune_levels(64, 4, 0, None, None, ctypes.byref(out_ms)) == binding.FMM_ERR_ARG
     L.fmm_batch_destroy(None)
+
+
+def test_fma_probe_counts_its_flops(lib):
+    # 1024 threads x 8 chains x 16 FMAs per trip x 2 flop
+    assert binding.lib().fmm_probe_fma_flops(3, 5) == 2.0 * 3 * 1024 * 5 * 16 * 8

@@ -4,6 +4,7 @@ import pytest
 
 from oracle import fmm as ofmm
 from paper_2011_07099_gb300 import inputs
+from parity_util import assert_close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -30,8 +31,8 @@ def test_leaf_size_six_matches_oracle(B):
     plan = B.Plan(N, L, p)
     phi, acc = plan.solve(torch.from_numpy(rho).cuda())
     ophi, og = ofmm.solve(rho, L, p)
-    assert _rel(phi.cpu().numpy(), ophi) <= 1e-6
-    assert _rel(acc.cpu().numpy(), og) <= 1e-6
+    assert_close(phi.cpu().numpy(), ophi, 1e-6, "batch field phi")
+    assert_close(acc.cpu().numpy(), og, 1e-6, "batch field g")
 
 
 @pytest.mark.parametrize("prec", [0, 2])

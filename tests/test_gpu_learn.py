@@ -3,8 +3,10 @@ differences of the oracle, and what training it gains."""
 import numpy as np
 import pytest
 
+from oracle import fmm as ofmm
 from oracle import learn as olearn
 from paper_2011_07099_gb300 import inputs
+from parity_util import assert_close, corner_and_interior_leaves, leaf_values
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -125,3 +127,51 @@ def test_bf16_inference_close_to_fp32_inference(B):
     assert corr_size > 0
     # BF16 inference perturbs the correction by ~2^-8 of its size
     assert np.linalg.norm(out[1][0] - out[0][0]) <= 2e-2 * corr_size
+
+
+@pytest.mark.parametrize("N,L,p", [(32, 3, 4), (64, 3, 6), (32, 5, 2)])
+def test_corrected_fp32_solve_matches_oracle_element_by_element(B, N, L, p):
+    # the forward solve with a (random, non-negligible) table correction, FP32
+    # inference and the plain FP32 form, against the oracle's FMM with the
+    # FP64 network evaluated at every n = o p + r - s of eq. fmm2
+    rho = inputs.lognormal(N, sigma=0.5, seed=40 + N + p)
+    w = _random_weights(11).astype(np.float32).astype(np.float64)
+    plan = B.Plan(N, L, p)
+    B.fmm_plan_set_correction_inference(plan.handle, B.FMM_INFER_FP32)
+    B.fmm_plan_set_correction(plan.handle, torch.from_numpy(w.astype(np.float32)).cuda())
+    phi, acc = plan.solve(torch.from_numpy(rho).cuda())
+    torch.cuda.synchronize()
+    plan.close()
+    ophi, og = ofmm.solve(rho, L, p, correction=olearn.correction_fn(w))
+    plain_phi, plain_g = ofmm.solve(rho, L, p)
+    # the correction moves the solution far beyond the tolerance ...
+    assert np.linalg.norm(plain_phi - ophi) > 1e-4 * np.linalg.norm(ophi)
+    # ... and the GPU follows the oracle element by element
+    assert_close(phi.cpu().numpy(), ophi, 1e-6, f"corrected phi {N}^3 L={L} p={p}")
+    assert_close(acc.cpu().numpy(), og, 1e-6, f"corrected g {N}^3 L={L} p={p}")
+
+
+def test_headline_form_with_shipped_weights_matches_oracle_at_sampled_leaves(B):
+    # exactly the form the bench times at 256^3 p = 6: bf16x3 tensor-core M2L,
+    # the shipped order-6 correction with BF16 inference, against the oracle's
+    # FMM with the same weights (FP64 network) at the 8 corner leaves and 2
+    # interior ones.  Bound: the bf16x3 tolerance 2e-5; BF16 inference
+    # perturbs the correction by ~2^-8 of its size, and the correction itself
+    # moves these fields by well under 1e-3, so its share is below 1e-5.
+    from paper_2011_07099_gb300 import learn
+    N, L, p = 256, 5, 6
+    w = learn.shipped_weights(p)
+    assert w is not None
+    rho = inputs.config_density(5, n=N)
+    plan = B.Plan(N, L, p)
+    plan.set_precision(B.FMM_PREC_BF16X3)
+    B.fmm_plan_set_correction(plan.handle, torch.from_numpy(w.astype(np.float32)).cuda())
+    phi, acc = plan.solve(torch.from_numpy(rho).cuda())
+    torch.cuda.synchronize()
+    assert B.lib().fmm_plan_check(plan.handle) == B.FMM_OK
+    plan.close()
+    leaves = corner_and_interior_leaves(L, 2, seed=66)
+    ref = ofmm.solve_at(rho, L, p, leaves, correction=olearn.correction_fn(w.astype(np.float64)))
+    got = leaf_values(phi.cpu().numpy(), acc.cpu().numpy(), leaves, N >> L)
+    assert_close(got[:, 0], ref[:, 0], 2e-5, "headline form phi, sampled leaves")
+    assert_close(got[:, 1:], ref[:, 1:], 2e-5, "headline form g, sampled leaves")

@@ -11,6 +11,7 @@ import pytest
 from oracle import fmm as ofmm
 from oracle import green, pm
 from paper_2011_07099_gb300 import inputs
+from parity_util import assert_close, corner_and_interior_leaves, leaf_values
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -77,9 +78,8 @@ def test_fp32_solve_matches_oracle(B, N, L, p, recipe):
     rho = _density(N, recipe, seed=N * 10 + L)
     plan, phi, acc = _gpu_solve(B, rho, L, p)
     ophi, og = ofmm.solve(rho, L, p)
-    e_phi, e_g = _rel(phi, ophi), _rel(acc, og)
-    assert e_phi <= TOL_FP32, e_phi
-    assert e_g <= TOL_FP32, e_g
+    assert_close(phi, ophi, TOL_FP32, f"phi {N}^3 L={L} p={p}")
+    assert_close(acc, og, TOL_FP32, f"g {N}^3 L={L} p={p}")
     plan.close()
 
 
@@ -97,10 +97,10 @@ def test_stage_buffers_match_oracle(B, N, L, p):
         n = 2 ** lev
         gm = plan.stage(B.FMM_STAGE_MULTIPOLE, lev).cpu().numpy().reshape(8 ** lev, p ** 3)
         om = M[lev].reshape(n ** 3, p ** 3)
-        assert _rel(gm[key], om) <= TOL_FP32, ("multipole", lev)
+        assert_close(gm[key], om, TOL_FP32, f"multipoles level {lev}")
         gf = plan.stage(B.FMM_STAGE_LOCAL, lev).cpu().numpy().reshape(8 ** lev, 4, p ** 3)
         of = F[lev].reshape(n ** 3, 4, p ** 3)
-        assert _rel(gf[key], of) <= TOL_FP32, ("local", lev)
+        assert_close(gf[key], of, TOL_FP32, f"local fields level {lev}")
     plan.close()
 
 
@@ -115,8 +115,8 @@ def test_corner_point_source(B):
     rho = inputs.point(32)
     plan, phi, acc = _gpu_solve(B, rho, 3, 4)
     ophi, og = ofmm.solve(rho, 3, 4)
-    assert _rel(phi, ophi) <= TOL_FP32
-    assert _rel(acc, og) <= TOL_FP32
+    assert_close(phi, ophi, TOL_FP32, "corner source phi")
+    assert_close(acc, og, TOL_FP32, "corner source g")
     # zero net force on the whole mesh (G odd gradient)
     m = pm.masses(rho.astype(np.float64))
     f = (m[None] * acc.astype(np.float64)).sum(axis=(1, 2, 3))
@@ -152,43 +152,42 @@ def test_bad_pointers_are_rejected(B):
 
 
 FULL = [
-    # (N, L, p, config, sampled leaves (z, y, x)): the 256^3 p = 6 headline
-    # workload and the 128^3 p = 4 Plummer-clump workload at full size, in the
-    # launch configuration the bench times; the oracle evaluates only the
-    # sampled leaves (whole upward pass, then each leaf's chain of ancestors).
-    (256, 5, 6, 5, [[0, 0, 0], [31, 31, 31], [5, 17, 30]]),
-    (128, 5, 4, 1, [[0, 0, 0], [31, 31, 31], [7, 20, 13]]),
+    # (N, L, p, config): the 256^3 p = 6 headline workload and the 128^3
+    # p = 4 Plummer-clump workload at full size, in the launch configuration
+    # the bench times; the oracle evaluates only the sampled leaves (whole
+    # upward pass, then each leaf's chain of ancestors): the 8 corner leaves,
+    # where every periodic wrap is taken, and 2 interior leaves.
+    (256, 5, 6, 5),
+    (128, 5, 4, 1),
     # the clustered order-8 recipe (1 + lognormal sigma 1.5 + Plummer clumps)
     # at 256^3, S = p = 8: the high-order precision path (FP64 masses and
     # local fields, double-float M2L at every level above the leaves)
-    (256, 5, 8, 4, [[1, 2, 3], [15, 0, 31]]),
+    (256, 5, 8, 4),
 ]
 
 
-@pytest.mark.parametrize("N,L,p,cfg,leaves", FULL)
-def test_full_size_sampled_leaves_match_oracle(B, N, L, p, cfg, leaves):
+@pytest.mark.parametrize("N,L,p,cfg", FULL)
+def test_full_size_sampled_leaves_match_oracle(B, N, L, p, cfg):
     if cfg == 4:   # the clump recipe is evaluated on the device (4096 clumps)
         rho = inputs.config_density_torch(cfg, torch.device("cuda", 0), n=N).cpu().numpy()
     else:
         rho = inputs.config_density(cfg, n=N)
     plan, phi, acc = _gpu_solve(B, rho, L, p)
-    leaves = np.array(leaves)
+    leaves = corner_and_interior_leaves(L, 2, seed=N + p)
     ref = ofmm.solve_at(rho, L, p, leaves)
-    S = N >> L
-    g = np.concatenate([phi[None], acc])
-    got = np.stack([g[:, a * S:(a + 1) * S, b * S:(b + 1) * S, c * S:(c + 1) * S].reshape(4, -1)
-                    for a, b, c in leaves])
-    assert _rel(got[:, 0], ref[:, 0]) <= TOL_FP32
-    assert _rel(got[:, 1:], ref[:, 1:]) <= TOL_FP32
+    got = leaf_values(phi, acc, leaves, N >> L)
+    assert_close(got[:, 0], ref[:, 0], TOL_FP32, f"phi {N}^3 p={p} sampled leaves")
+    assert_close(got[:, 1:], ref[:, 1:], TOL_FP32, f"g {N}^3 p={p} sampled leaves")
     plan.close()
 
 
 def test_full_scale_512_order8_sampled_leaves(B):
     # the full-scale workload exactly as bench.py --workload full512 runs it
     # (512^3, p = 8, L = 6, clustered recipe on the device), plain and mixed
-    # forms against the oracle at two sampled leaves (one oracle evaluation)
+    # forms against the oracle at the 8 corner leaves and 2 interior ones
+    # (one oracle evaluation)
     N, L, p = 512, 6, 8
-    leaves = np.array([[1, 2, 3], [40, 0, 63]])
+    leaves = corner_and_interior_leaves(L, 2, seed=512)
     rho_t = inputs.config_density_torch(4, torch.device("cuda", 0), n=N)
     rho = rho_t.cpu().numpy()
     ref = ofmm.solve_at(rho, L, p, leaves)
@@ -205,6 +204,5 @@ def test_full_scale_512_order8_sampled_leaves(B):
                         for a, b, c in leaves])
         plan.close()
         del phi, acc
-        e_phi, e_g = _rel(got[:, 0], ref[:, 0]), _rel(got[:, 1:], ref[:, 1:])
-        print(f"512^3 p=8 precision {prec}: phi {e_phi:.3e} g {e_g:.3e}")
-        assert e_phi <= tol and e_g <= tol
+        assert_close(got[:, 0], ref[:, 0], tol, f"512^3 p=8 precision {prec} phi")
+        assert_close(got[:, 1:], ref[:, 1:], tol, f"512^3 p=8 precision {prec} g")

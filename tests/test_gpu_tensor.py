@@ -16,6 +16,7 @@ import pytest
 from oracle import fmm as ofmm
 from oracle import green, pm
 from paper_2011_07099_gb300 import inputs
+from parity_util import assert_close, corner_and_interior_leaves, leaf_values
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -56,8 +57,8 @@ def test_bf16x3_matches_oracle(B, N, L, p):
     rho = inputs.lognormal(N, sigma=0.5, seed=N + L + p)
     phi, acc = _solve(B, rho, L, p, B.FMM_PREC_BF16X3)
     ophi, og = ofmm.solve(rho, L, p)
-    assert _rel(phi, ophi) <= TOL_BF16X3
-    assert _rel(acc, og) <= TOL_BF16X3
+    assert_close(phi, ophi, TOL_BF16X3, f"bf16x3 phi {N}^3 L={L} p={p}")
+    assert_close(acc, og, TOL_BF16X3, f"bf16x3 g {N}^3 L={L} p={p}")
 
 
 @pytest.mark.parametrize("group", [1, 3, 189])
@@ -69,39 +70,40 @@ def test_bf16x3_promotion_group_sizes(B, group):
     phi, acc = _solve(B, rho, L, p, B.FMM_PREC_BF16X3, group)
     ophi, og = ofmm.solve(rho, L, p)
     tol = TOL_BF16X3 if group <= 3 else 1e-3
-    assert _rel(phi, ophi) <= tol
-    assert _rel(acc, og) <= tol
+    assert_close(phi, ophi, tol, f"group {group} phi")
+    assert_close(acc, og, tol, f"group {group} g")
 
 
-def test_bf16_matches_oracle(B):
-    N, L, p = 64, 4, 4
-    rho = inputs.lognormal(N, sigma=0.5, seed=1)
+@pytest.mark.parametrize("N,L,p,recipe", [(64, 4, 4, "lognormal"), (32, 3, 3, "plummer"), (64, 5, 2, "lognormal")])
+def test_bf16_matches_oracle(B, N, L, p, recipe):
+    if recipe == "plummer":
+        rho = inputs.plummer(N, n_clumps=8, seed=N + p)
+    else:
+        rho = inputs.lognormal(N, sigma=0.5, seed=N + p)
     phi, acc = _solve(B, rho, L, p, B.FMM_PREC_BF16)
     ophi, og = ofmm.solve(rho, L, p)
-    assert _rel(phi, ophi) <= TOL_BF16
-    assert _rel(acc, og) <= TOL_BF16
+    assert_close(phi, ophi, TOL_BF16, f"bf16 phi {N}^3 L={L} p={p}")
+    assert_close(acc, og, TOL_BF16, f"bf16 g {N}^3 L={L} p={p}")
 
 
-@pytest.mark.parametrize("N,L,p,cfg,leaves", [
-    (256, 5, 6, 5, [[0, 0, 0], [31, 31, 31], [5, 17, 30]]),
-    (128, 5, 4, 1, [[0, 0, 0], [31, 31, 31], [7, 20, 13]]),
+@pytest.mark.parametrize("N,L,p,cfg", [
+    (256, 5, 6, 5),
+    (128, 5, 4, 1),
     # order 8, clustered recipe: only the leaf level runs on the tensor cores
-    (256, 5, 8, 4, [[1, 2, 3], [15, 0, 31]]),
+    (256, 5, 8, 4),
 ])
-def test_bf16x3_full_size_sampled(B, N, L, p, cfg, leaves):
+def test_bf16x3_full_size_sampled(B, N, L, p, cfg):
+    # the 8 corner leaves (every periodic wrap) and 2 interior ones
     if cfg == 4:   # the clump recipe is evaluated on the device (4096 clumps)
         rho = inputs.config_density_torch(cfg, torch.device("cuda", 0), n=N).cpu().numpy()
     else:
         rho = inputs.config_density(cfg, n=N)
     phi, acc = _solve(B, rho, L, p, B.FMM_PREC_BF16X3)
-    leaves = np.array(leaves)
+    leaves = corner_and_interior_leaves(L, 2, seed=N + p + 1)
     ref = ofmm.solve_at(rho, L, p, leaves)
-    S = N >> L
-    g = np.concatenate([phi[None], acc])
-    got = np.stack([g[:, a * S:(a + 1) * S, b * S:(b + 1) * S, c * S:(c + 1) * S].reshape(4, -1)
-                    for a, b, c in leaves])
-    assert _rel(got[:, 0], ref[:, 0]) <= TOL_BF16X3
-    assert _rel(got[:, 1:], ref[:, 1:]) <= TOL_BF16X3
+    got = leaf_values(phi, acc, leaves, N >> L)
+    assert_close(got[:, 0], ref[:, 0], TOL_BF16X3, f"bf16x3 phi {N}^3 p={p} sampled leaves")
+    assert_close(got[:, 1:], ref[:, 1:], TOL_BF16X3, f"bf16x3 g {N}^3 p={p} sampled leaves")
 
 
 def test_mixed_form_within_1e4_of_pm_at_256(B):
@@ -138,6 +140,6 @@ def test_bounded_wait_expires_and_context_survives(B, limit_ms):
     for _ in range(2):
         phi, acc = plan.solve(d)
         assert B.lib().fmm_plan_check(plan.handle) == B.FMM_OK
-        assert _rel(phi.cpu().numpy(), ophi) <= TOL_BF16X3
-        assert _rel(acc.cpu().numpy(), og) <= TOL_BF16X3
+        assert_close(phi.cpu().numpy(), ophi, TOL_BF16X3, "after timeout phi")
+        assert_close(acc.cpu().numpy(), og, TOL_BF16X3, "after timeout g")
     plan.close()
