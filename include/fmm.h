@@ -316,6 +316,37 @@ int fmm_plan_error_stats(fmm_plan* plan, const float* density, const float* pote
                          const float* accel, int samples, unsigned long long seed,
                          double* out, void* stream);
 
+/* ---- grid model of G_* --------------------------------------------------- */
+/* Sec. 4's other proposal: parameterise G_* as a grid of values, every value
+ * its own parameter.  Here each level l = 2..L carries one free value per
+ * folded table entry and field: theta[l - 2][f][az][ay][ax] with a_i in
+ * [0, 4p) (the (4 N_g)^3 samples Sec. 4 counts), f = 0 for G and 1..3 for
+ * -dG/dx, -dG/dy, -dG/dz.  The M2L table entry at offset n (gridlet units,
+ * taken to its nearest periodic image) becomes G_S1 + theta[0][|n|] for G
+ * and -dG/dx_i + sign(n_i) theta[i][|n|] for the gradients (sign 0 at half
+ * the box), so the table keeps the parity and periodicity of G_S1 and the
+ * solve keeps zero net force.  The near zone keeps the exact G_S1.  The
+ * grid adds to the MLP correction when both are set. */
+
+/* Number of grid parameters of the plan: (L - 1) x 4 x (4 order)^3. */
+int fmm_plan_table_grid_size(const fmm_plan* plan, size_t* n);
+
+/* Set (theta = device or host pointer to fmm_plan_table_grid_size floats,
+ * copied) or clear (theta = NULL) the grid and re-tabulate every M2L table
+ * form (synchronous).  FMM_ERR_ARG if n is not the plan's grid size. */
+int fmm_plan_set_table_grid(fmm_plan* plan, const float* theta, size_t n);
+
+/* One training field for the grid model: solve `density` with the current
+ * tables, compare with the target solution (device, N^3 potential and 3 N^3
+ * acceleration) and ADD to `grad` (device, grid-size floats) the gradient of
+ * J = w_phi |Phi - Phi*|^2 + w_g |g - g*|^2 with respect to theta, and J to
+ * `loss` (device, 1 float): the adjoint of L2P and L2L, the table gradient
+ * of eq. fmm2 and its fold onto the grid entries, all on the GPU.  Enqueued
+ * on `stream`.  A grid need not be set (the gradient is then taken at
+ * theta = 0). */
+int fmm_table_grid_grad(fmm_plan* plan, const float* density, const float* target_phi, const float* target_acc,
+                        float w_phi, float w_g, float* grad, float* loss, void* stream);
+
 /* ---- measurement aid ----------------------------------------------------- */
 
 /* FP32 FMA throughput probe; the paper has no counterpart.  Enqueues on

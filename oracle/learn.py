@@ -112,6 +112,12 @@ def correction_fn(w):
     of the interaction zones has |o_i| <= 3, so every such n lies in the cube
     |n_i| <= 4p - 1: the correction is evaluated once per (level, p) on that
     cube and looked up."""
+    return _matrices_from(lambda level, p, n: table_correction(w, level, p, n))
+
+
+def _matrices_from(entry_fn):
+    """(level, p, offset) -> (4, p^3, p^3) matrices of a per-entry table
+    correction entry_fn(level, p, n (k, 3)) -> (k, 4)."""
     tables = {}
 
     def corr(level, p, off_zyx):
@@ -120,7 +126,7 @@ def correction_fn(w):
             g = np.arange(-h, h + 1)
             nz, ny, nx = np.meshgrid(g, g, g, indexing="ij")
             cube = np.stack([nx.ravel(), ny.ravel(), nz.ravel()], axis=-1)     # x fastest
-            tables[(level, p)] = table_correction(w, level, p, cube).reshape(2 * h + 1, 2 * h + 1, 2 * h + 1, 4)
+            tables[(level, p)] = entry_fn(level, p, cube).reshape(2 * h + 1, 2 * h + 1, 2 * h + 1, 4)
         tab = tables[(level, p)]
         g = np.arange(p)
         z, y, x = np.meshgrid(g, g, g, indexing="ij")
@@ -132,6 +138,49 @@ def correction_fn(w):
         return np.moveaxis(c, -1, 0)
 
     return corr
+
+
+# ------------------------------------------------------- grid model of G_*
+# Sec. 4: G_* as a grid of values, each its own parameter.  Per level
+# l = 2..L, theta[l - 2] has shape (4, 4p, 4p, 4p) = [f][a_z][a_y][a_x]: the
+# table entry at offset n (gridlet units) gets theta[0][a] added to G and
+# sign(n_i) theta[i][a] added to -dG/dx_i, with a = |n| component-wise after
+# taking n to its nearest periodic image (period 2^l p), and the gradient
+# sign 0 at half the period.
+
+def grid_size(L, p):
+    return (L - 1) * 4 * (4 * p) ** 3
+
+
+def grid_table_correction(theta, level, p, n):
+    """(k, 4) grid corrections of the table entries with offsets n (k, 3);
+    theta: the flat parameters of all levels (grid_size(L, p) values)."""
+    G = 4 * p
+    blk = np.asarray(theta, dtype=np.float64).reshape(-1, 4, G, G, G)[level - 2]
+    n = np.asarray(n, dtype=np.int64)
+    period = 2 ** level * p
+    wn = np.mod(n, period)
+    wn = np.where(2 * wn > period, wn - period, wn)
+    a = np.abs(wn)
+    sg = np.sign(wn).astype(np.float64)
+    sg[2 * a == period] = 0.0
+    out = np.empty((len(n), 4))
+    out[:, 0] = blk[0, a[:, 2], a[:, 1], a[:, 0]]
+    for f in range(1, 4):
+        out[:, f] = sg[:, f - 1] * blk[f, a[:, 2], a[:, 1], a[:, 0]]
+    out[np.all(n == 0, axis=1)] = 0.0
+    return out
+
+
+def grid_correction_fn(theta):
+    """The grid model as a ``correction`` for ``fmm.solve``."""
+    return _matrices_from(lambda level, p, n: grid_table_correction(theta, level, p, n))
+
+
+def grid_loss(theta, rho, L, p, target_phi, target_g, w_phi, w_g):
+    """J of ``loss`` for the FMM with the grid-corrected tables (FP64)."""
+    phi, g = fmm.solve(rho, L, p, correction=grid_correction_fn(theta))
+    return float(w_phi * np.sum((phi - target_phi) ** 2) + w_g * np.sum((g - target_g) ** 2))
 
 
 def loss(w, rho, L, p, target_phi, target_g, w_phi, w_g):

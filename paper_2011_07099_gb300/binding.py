@@ -56,6 +56,9 @@ SIGNATURES = {
     "fmm_plan_inject_fault": (_I, [_VP, _I]),
     "fmm_mean_density_noalloc": (_I, [_FP, _SZ, _FP, _VP]),
     "fmm_probe_fma": (_I, [_FP, _I, _I, _VP]),
+    "fmm_plan_table_grid_size": (_I, [_VP, ctypes.POINTER(_SZ)]),
+    "fmm_plan_set_table_grid": (_I, [_VP, _FP, _SZ]),
+    "fmm_table_grid_grad": (_I, [_VP, _FP, _FP, _FP, ctypes.c_float, ctypes.c_float, _FP, _FP, _VP]),
     "fmm_probe_fma_flops": (ctypes.c_double, [_I, _I]),
     "fmm_plan_set_correction": (_I, [_VP, _FP, _SZ]),
     "fmm_plan_set_correction_inference": (_I, [_VP, _I]),
@@ -204,6 +207,25 @@ def fmm_adam_step(weights, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-
 
 def fmm_mesh_green(N, out, stream=None):
     _check(lib().fmm_mesh_green(int(N), out.data_ptr(), _stream_of(out, stream)), "fmm_mesh_green")
+
+
+def fmm_plan_table_grid_size(plan):
+    n = _SZ(0)
+    _check(lib().fmm_plan_table_grid_size(plan, ctypes.byref(n)), "fmm_plan_table_grid_size")
+    return int(n.value)
+
+
+def fmm_plan_set_table_grid(plan, theta):
+    if theta is None:
+        _check(lib().fmm_plan_set_table_grid(plan, None, 0), "fmm_plan_set_table_grid")
+    else:
+        _check(lib().fmm_plan_set_table_grid(plan, theta.data_ptr(), theta.numel()), "fmm_plan_set_table_grid")
+
+
+def fmm_table_grid_grad(plan, density, target_phi, target_acc, w_phi, w_g, grad, loss, stream=None):
+    _check(lib().fmm_table_grid_grad(plan, density.data_ptr(), target_phi.data_ptr(), target_acc.data_ptr(),
+                                     float(w_phi), float(w_g), grad.data_ptr(), loss.data_ptr(),
+                                     _stream_of(density, stream)), "fmm_table_grid_grad")
 
 
 def fmm_probe_fma(out, blocks, iters, stream=None):

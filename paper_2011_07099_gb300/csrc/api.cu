@@ -109,6 +109,7 @@ void free_plan(Plan* P) {
   cudaFree(P->lam_cells);
   cudaFree(P->dT_all);
   cudaFree(P->grad_partials);
+  cudaFree(P->grid);
   for (int l = 0; l <= fmm::kMaxLevel; ++l) cudaFree(P->lam[l]);
   for (int l = 0; l <= fmm::kMaxLevel; ++l) {
     cudaFree(P->tab_bf[l]);
@@ -128,6 +129,45 @@ void free_plan(Plan* P) {
 template <typename T>
 bool dev_alloc(T** ptr, size_t count) {
   return cudaMalloc(reinterpret_cast<void**>(ptr), sizeof(T) * count) == cudaSuccess;
+}
+
+// Re-tabulate every table form from G_S1 plus the plan's corrections (MLP,
+// grid), synchronously.  Returns an FMM_* code.
+int retabulate(Plan& P) {
+  if (fmm::launch_tables(P, 0) != cudaSuccess) return FMM_ERR_CUDA;
+  if (P.tc_ready) {
+    for (int l = fmm::kTcMinLevel; l <= P.L; ++l) {
+      if (!P.Apre[l]) continue;
+      if (fmm::launch_tab_bf16(P, l, 0) != cudaSuccess || fmm::launch_build_a(P, l, 0) != cudaSuccess)
+        return FMM_ERR_CUDA;
+    }
+  }
+  return cudaDeviceSynchronize() == cudaSuccess ? FMM_OK : FMM_ERR_CUDA;
+}
+
+// Training buffers (first use) and one forward solve, cell residual and
+// adjoint sweep down to the table gradients P.dT of every level; the loss is
+// added to `loss`.  Returns an FMM_* code.
+int table_gradient(Plan& P, const float* density, const float* target_phi, const float* target_acc, float w_phi,
+                   float w_g, float* loss, void* stream) {
+  const size_t n3 = (size_t)P.N * P.N * P.N;
+  const size_t p3 = (size_t)P.p * P.p * P.p, E = 8 * P.p - 1;
+  if (!P.train_out) {
+    bool ok = dev_alloc(&P.train_out, 4 * n3) && dev_alloc(&P.lam_cells, 4 * n3) &&
+              dev_alloc(&P.dT_all, (size_t)(P.L - 1) * E * E * E * 4) &&
+              dev_alloc(&P.grad_partials, (size_t)fmm::mlp_backward_blocks(P) * fmm::mlp::kParams);
+    for (int l = 2; l <= P.L && ok; ++l) ok = dev_alloc(&P.lam[l], ((size_t)1 << (3 * l)) * 4 * p3);
+    if (!ok) return FMM_ERR_ALLOC;
+    for (int l = 2; l <= P.L; ++l) P.dT[l] = P.dT_all + (size_t)(l - 2) * E * E * E * 4;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int rc = fmm_solve(reinterpret_cast<fmm_plan*>(&P), density, P.train_out, P.train_out + n3, stream);
+  if (rc != FMM_OK) return rc;
+  if (fmm::launch_residual(P.train_out, P.train_out + n3, target_phi, target_acc, n3, w_phi, w_g, P.lam_cells, loss,
+                           P.num_sms, s) != cudaSuccess ||
+      fmm::launch_adjoint_and_table_grad(P, P.lam_cells, s) != cudaSuccess)
+    return FMM_ERR_CUDA;
+  return FMM_OK;
 }
 
 }  // namespace
@@ -366,17 +406,7 @@ int fmm_plan_set_correction(fmm_plan* plan, const float* weights, size_t n) {
   } else {
     P.has_corr = 0;
   }
-  // re-tabulate every table form from G_S1 (+ the correction)
-  FMM_CUDA_TRY(fmm::launch_tables(P, 0));
-  if (P.tc_ready) {
-    for (int l = fmm::kTcMinLevel; l <= P.L; ++l) {
-      if (!P.Apre[l]) continue;
-      FMM_CUDA_TRY(fmm::launch_tab_bf16(P, l, 0));
-      FMM_CUDA_TRY(fmm::launch_build_a(P, l, 0));
-    }
-  }
-  FMM_CUDA_TRY(cudaDeviceSynchronize());
-  return set_err(FMM_OK);
+  return set_err(retabulate(P));
 }
 
 int fmm_correction_grad(fmm_plan* plan, const float* density, const float* target_phi, const float* target_acc,
@@ -384,23 +414,41 @@ int fmm_correction_grad(fmm_plan* plan, const float* density, const float* targe
   if (!plan || !density || !target_phi || !target_acc || !grad || !loss) return set_err(FMM_ERR_ARG);
   Plan& P = *reinterpret_cast<Plan*>(plan);
   if (!P.has_corr) return set_err(FMM_ERR_ARG);
-  const size_t n3 = (size_t)P.N * P.N * P.N;
-  const size_t p3 = (size_t)P.p * P.p * P.p, E = 8 * P.p - 1;
-  if (!P.train_out) {
-    bool ok = dev_alloc(&P.train_out, 4 * n3) && dev_alloc(&P.lam_cells, 4 * n3) &&
-              dev_alloc(&P.dT_all, (size_t)(P.L - 1) * E * E * E * 4) &&
-              dev_alloc(&P.grad_partials, (size_t)fmm::mlp_backward_blocks(P) * fmm::mlp::kParams);
-    for (int l = 2; l <= P.L && ok; ++l) ok = dev_alloc(&P.lam[l], ((size_t)1 << (3 * l)) * 4 * p3);
-    if (!ok) return set_err(FMM_ERR_ALLOC);
-    for (int l = 2; l <= P.L; ++l) P.dT[l] = P.dT_all + (size_t)(l - 2) * E * E * E * 4;
+  const int rc = table_gradient(P, density, target_phi, target_acc, w_phi, w_g, loss, stream);
+  if (rc != FMM_OK) return set_err(rc);
+  FMM_CUDA_TRY(fmm::launch_mlp_backward(P, P.corr_w, grad, reinterpret_cast<cudaStream_t>(stream)));
+  return set_err(FMM_OK);
+}
+
+int fmm_plan_table_grid_size(const fmm_plan* plan, size_t* n) {
+  if (!plan || !n) return set_err(FMM_ERR_ARG);
+  const Plan& P = *reinterpret_cast<const Plan*>(plan);
+  *n = (size_t)(P.L - 1) * fmm::grid_level_size(P.p);
+  return set_err(FMM_OK);
+}
+
+int fmm_plan_set_table_grid(fmm_plan* plan, const float* theta, size_t n) {
+  if (!plan) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  const size_t need = (size_t)(P.L - 1) * fmm::grid_level_size(P.p);
+  if (theta) {
+    if (n != need) return set_err(FMM_ERR_ARG);
+    if (!P.grid && !dev_alloc(&P.grid, need)) return set_err(FMM_ERR_ALLOC);
+    FMM_CUDA_TRY(cudaMemcpy(P.grid, theta, need * sizeof(float), cudaMemcpyDefault));
+    P.has_grid = 1;
+  } else {
+    P.has_grid = 0;
   }
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  int rc = fmm_solve(plan, density, P.train_out, P.train_out + n3, stream);
-  if (rc != FMM_OK) return rc;
-  FMM_CUDA_TRY(fmm::launch_residual(P.train_out, P.train_out + n3, target_phi, target_acc, n3, w_phi, w_g, P.lam_cells,
-                                    loss, P.num_sms, s));
-  FMM_CUDA_TRY(fmm::launch_adjoint_and_table_grad(P, P.lam_cells, s));
-  FMM_CUDA_TRY(fmm::launch_mlp_backward(P, P.corr_w, grad, s));
+  return set_err(retabulate(P));
+}
+
+int fmm_table_grid_grad(fmm_plan* plan, const float* density, const float* target_phi, const float* target_acc,
+                        float w_phi, float w_g, float* grad, float* loss, void* stream) {
+  if (!plan || !density || !target_phi || !target_acc || !grad || !loss) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  const int rc = table_gradient(P, density, target_phi, target_acc, w_phi, w_g, loss, stream);
+  if (rc != FMM_OK) return set_err(rc);
+  FMM_CUDA_TRY(fmm::launch_grid_grad(P, grad, reinterpret_cast<cudaStream_t>(stream)));
   return set_err(FMM_OK);
 }
 

@@ -104,6 +104,10 @@ struct Plan {
   float* dT_all = nullptr;                 // table gradients, levels 2..L, (8p-1)^3 x 4 each
   float* dT[kMaxLevel + 1] = {};
   float* grad_partials = nullptr;          // per-block MLP gradient partials
+  // grid model of G_* (Sec. 4): one free value per folded table entry and
+  // field, per level: levels 2..L x 4 fields x (4p)^3, added to the tables
+  float* grid = nullptr;
+  int has_grid = 0;
   uint64_t wait_ns = 2000000000ull;        // limit of every bounded device-side wait
   int inject_stall = 0;                    // test hook: tensor-core MMA issuer stalls
   int tc_ready = 0;
@@ -171,6 +175,10 @@ cudaError_t launch_error_stats(Plan& P, const float* rho, const float* phi, cons
                                const unsigned long long* targets, int T, double* partials, double* sums,
                                double* mean_scratch, cudaStream_t s);
 cudaError_t launch_tab_bf16(Plan& P, int level, cudaStream_t s);
+// Grid-model parameters per level: 4 fields x (4p)^3 folded entries.
+inline size_t grid_level_size(int p) { return (size_t)4 * (4 * p) * (4 * p) * (4 * p); }
+// dJ/d(grid) += the table gradients P.dT folded onto the grid's entries.
+cudaError_t launch_grid_grad(Plan& P, float* grad, cudaStream_t s);
 cudaError_t launch_split_bf16(Plan& P, int level, cudaStream_t s);
 cudaError_t launch_m2l_tc(Plan& P, int level, int mode, cudaStream_t s);
 int tc_padded_k(int p);

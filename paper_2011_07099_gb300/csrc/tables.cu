@@ -28,12 +28,36 @@ __device__ inline void add_correction(double v[4], int ix, int iy, int iz, int l
   }
 }
 
+// Grid model of G_* (Sec. 4: every table value its own parameter).  The
+// parameters sit on the folded entries: the offset is taken to its nearest
+// periodic image (the level-l box spans 2^l p gridlet spacings) and folded
+// over the sign of each component; G adds grid[0][a], -dG/dx_i adds
+// sign(n_i) grid[i][a] (zero at half the box, where the odd periodic
+// gradient vanishes), so the corrected table keeps the parity and the
+// periodicity of G_S1.  `grid` is this level's 4 x (4p)^3 block.
+__device__ inline void add_grid(double v[4], int ix, int iy, int iz, int level, int p, const float* grid) {
+  if (!grid || !(ix | iy | iz)) return;
+  const int period = (1 << level) * p, G = 4 * p;
+  const int n[3] = {ix, iy, iz};
+  int a[3];
+  double sg[3];
+  for (int i = 0; i < 3; ++i) {
+    int w = ((n[i] % period) + period) % period;
+    if (2 * w > period) w -= period;
+    a[i] = w < 0 ? -w : w;
+    sg[i] = 2 * a[i] == period ? 0.0 : (w > 0 ? 1.0 : (w < 0 ? -1.0 : 0.0));
+  }
+  const size_t e = ((size_t)a[2] * G + a[1]) * G + a[0], G3 = (size_t)G * G * G;
+  v[0] += (double)grid[e];
+  for (int f = 1; f < 4; ++f) v[f] += sg[f - 1] * (double)grid[f * G3 + e];
+}
+
 // M2L table of level l: n in [-(4p-1), 4p-1]^3 at spacing dx_l = 1/(2^l p)
 // (Sec. 3: gridlet spacing of a level-l node; the (4 N_g)^D samples of Sec. 4
 // folded over the sign of each component).  Entry n = 0 is never used by M2L
 // (the interaction zone excludes near nodes) and is stored as 0.
 __global__ void k_tab_m2l(float4* __restrict__ out, float4* __restrict__ lo, int p, int level, const float* mlp,
-                          int fp32) {
+                          int fp32, const float* grid) {
   const int hw = 4 * p - 1, E = 8 * p - 1;
   const long total = (long)E * E * E;
   const double dx = 1.0 / ((double)(1 << level) * p);
@@ -42,6 +66,7 @@ __global__ void k_tab_m2l(float4* __restrict__ out, float4* __restrict__ lo, int
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (ix | iy | iz) gs1(ix * dx, iy * dx, iz * dx, v);
     add_correction(v, ix, iy, iz, level, p, mlp, fp32);
+    add_grid(v, ix, iy, iz, level, p, grid);
     out[i] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
     if (lo)
       lo[i] = make_float4((float)(v[0] - (double)(float)v[0]), (float)(v[1] - (double)(float)v[1]),
@@ -74,7 +99,7 @@ __global__ void k_tab_near(float4* __restrict__ out, int S, int N) {
 // The same level table split into BF16 hi + lo per field for the tensor-core
 // M2L: each uint32 holds hi in its low half and lo = bf16(v - hi) in its high
 // half, the four fields in the four words of a uint4.
-__global__ void k_tab_bf16(uint4* __restrict__ out, int p, int level, const float* mlp, int fp32) {
+__global__ void k_tab_bf16(uint4* __restrict__ out, int p, int level, const float* mlp, int fp32, const float* grid) {
   const int hw = 4 * p - 1, E = 8 * p - 1;
   const long total = (long)E * E * E;
   const double dx = 1.0 / ((double)(1 << level) * p);
@@ -83,6 +108,7 @@ __global__ void k_tab_bf16(uint4* __restrict__ out, int p, int level, const floa
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (ix | iy | iz) gs1(ix * dx, iy * dx, iz * dx, v);
     add_correction(v, ix, iy, iz, level, p, mlp, fp32);
+    add_grid(v, ix, iy, iz, level, p, grid);
     uint32_t w[4];
     for (int f = 0; f < 4; ++f) {
       const __nv_bfloat16 h = __double2bfloat16(v[f]);
@@ -93,18 +119,58 @@ __global__ void k_tab_bf16(uint4* __restrict__ out, int p, int level, const floa
   }
 }
 
+// Gradient of the grid parameters of one level from the table gradient dT
+// (layout [n][f], n over the (8p-1)^3 table): every table entry adds its
+// gradient, times the sign it was applied with, to the entry it folds onto.
+__global__ void k_grid_grad(const float* __restrict__ dT, int p, int level, float* __restrict__ g) {
+  const int hw = 4 * p - 1, E = 8 * p - 1, period = (1 << level) * p, G = 4 * p;
+  const long total = (long)E * E * E * 4;
+  const size_t G3 = (size_t)G * G * G;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const int f = (int)(i % 4);
+    const long e = i / 4;
+    const int n[3] = {(int)(e % E) - hw, (int)((e / E) % E) - hw, (int)(e / ((long)E * E)) - hw};
+    if (!(n[0] | n[1] | n[2])) continue;
+    int a[3];
+    float sg[3];
+    for (int k = 0; k < 3; ++k) {
+      int w = ((n[k] % period) + period) % period;
+      if (2 * w > period) w -= period;
+      a[k] = w < 0 ? -w : w;
+      sg[k] = 2 * a[k] == period ? 0.f : (w > 0 ? 1.f : (w < 0 ? -1.f : 0.f));
+    }
+    const float sgn = f == 0 ? 1.f : sg[f - 1];
+    const float d = dT[i];
+    if (sgn == 0.f || d == 0.f) continue;
+    atomicAdd(&g[f * G3 + ((size_t)a[2] * G + a[1]) * G + a[0]], sgn * d);
+  }
+}
+
+const float* grid_of(const Plan& P, int level) {
+  return P.has_grid ? P.grid + (size_t)(level - 2) * grid_level_size(P.p) : nullptr;
+}
+
 }  // namespace
+
+cudaError_t launch_grid_grad(Plan& P, float* grad, cudaStream_t s) {
+  for (int l = 2; l <= P.L; ++l) {
+    k_grid_grad<<<4 * P.num_sms, 256, 0, s>>>(P.dT[l], P.p, l, grad + (size_t)(l - 2) * grid_level_size(P.p));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 cudaError_t launch_tab_bf16(Plan& P, int level, cudaStream_t s) {
   k_tab_bf16<<<4 * P.num_sms, 256, 0, s>>>(P.tab_bf[level], P.p, level, P.has_corr ? P.corr_w : nullptr,
-                                           P.corr_fp32);
+                                           P.corr_fp32, grid_of(P, level));
   return cudaGetLastError();
 }
 
 cudaError_t launch_tables(Plan& P, cudaStream_t s) {
   for (int l = 2; l <= P.L; ++l) {
     k_tab_m2l<<<4 * P.num_sms, 256, 0, s>>>(P.tab[l], P.tab_lo[l], P.p, l, P.has_corr ? P.corr_w : nullptr,
-                                            P.corr_fp32);
+                                            P.corr_fp32, grid_of(P, l));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -66,21 +66,39 @@ def init_weights(seed):
 
 
 class Trainer:
-    """Adam on the correction's weights; state = (weights, m, v, step)."""
+    """Adam on the parameters of a table model; state = (params, m, v, step).
 
-    def __init__(self, N, L, p, seed=0, lr=1e-3, device="cuda"):
+    model = "mlp": the learned correction's network weights
+    (fmm_plan_set_correction / fmm_correction_grad); model = "grid": the grid
+    model of G_* of Sec. 4, one value per folded table entry and field
+    (fmm_plan_set_table_grid / fmm_table_grid_grad), starting at zero (the
+    plain G_S1 tables)."""
+
+    def __init__(self, N, L, p, seed=0, lr=1e-3, device="cuda", model="mlp"):
         import torch
-        self.N, self.L, self.p, self.lr = N, L, p, lr
+        self.N, self.L, self.p, self.lr, self.model = N, L, p, lr, model
         self.device = torch.device(device)
         self.plan = B.Plan(N, L, p)
-        B.fmm_plan_set_correction_inference(self.plan.handle, B.FMM_INFER_FP32)
-        self.w = torch.from_numpy(init_weights(seed)).to(self.device)
+        if model == "mlp":
+            B.fmm_plan_set_correction_inference(self.plan.handle, B.FMM_INFER_FP32)
+            self.w = torch.from_numpy(init_weights(seed)).to(self.device)
+        elif model == "grid":
+            self.w = torch.zeros(B.fmm_plan_table_grid_size(self.plan.handle), dtype=torch.float32,
+                                 device=self.device)
+        else:
+            raise ValueError(model)
         self.m = torch.zeros_like(self.w)
         self.v = torch.zeros_like(self.w)
         self.grad = torch.zeros_like(self.w)
         self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
         self.step_count = 0
-        B.fmm_plan_set_correction(self.plan.handle, self.w)
+        self._apply()
+
+    def _apply(self):
+        if self.model == "mlp":
+            B.fmm_plan_set_correction(self.plan.handle, self.w)
+        else:
+            B.fmm_plan_set_table_grid(self.plan.handle, self.w)
 
     def prepare(self, density_np):
         """Device density, PM target and the relative-error weights of a field."""
@@ -96,12 +114,13 @@ class Trainer:
         the mean loss before the update."""
         self.grad.zero_()
         self.loss.zero_()
+        grad_fn = B.fmm_correction_grad if self.model == "mlp" else B.fmm_table_grid_grad
         for d, tphi, tacc, w_phi, w_g in batch:
-            B.fmm_correction_grad(self.plan.handle, d, tphi, tacc, w_phi, w_g, self.grad, self.loss)
+            grad_fn(self.plan.handle, d, tphi, tacc, w_phi, w_g, self.grad, self.loss)
         self.grad /= len(batch)
         self.step_count += 1
         B.fmm_adam_step(self.w, self.grad, self.m, self.v, self.step_count, self.lr)
-        B.fmm_plan_set_correction(self.plan.handle, self.w)
+        self._apply()
         return float(self.loss.item()) / len(batch)
 
     def state(self):
@@ -118,7 +137,7 @@ class Trainer:
         self.m.copy_(torch.from_numpy(z["m"]))
         self.v.copy_(torch.from_numpy(z["v"]))
         self.step_count = int(z["step"])
-        B.fmm_plan_set_correction(self.plan.handle, self.w)
+        self._apply()
 
 
 def relative_errors(plan, d, tphi, tacc):
@@ -141,8 +160,9 @@ def main():
     ap.add_argument("--seed", type=int, default=3000)
     ap.add_argument("--out", default="correction.npz")
     ap.add_argument("--resume", default=None)
+    ap.add_argument("--model", choices=["mlp", "grid"], default="mlp")
     args = ap.parse_args()
-    tr = Trainer(args.n, args.L, args.p, seed=args.seed, lr=args.lr)
+    tr = Trainer(args.n, args.L, args.p, seed=args.seed, lr=args.lr, model=args.model)
     if args.resume:
         tr.load(args.resume)
     fields = [tr.prepare(inputs.lognormal(args.n, sigma=0.5, seed=args.seed + i)) for i in range(args.fields)]

@@ -175,3 +175,87 @@ def test_headline_form_with_shipped_weights_matches_oracle_at_sampled_leaves(B):
     got = leaf_values(phi.cpu().numpy(), acc.cpu().numpy(), leaves, N >> L)
     assert_close(got[:, 0], ref[:, 0], 2e-5, "headline form phi, sampled leaves")
     assert_close(got[:, 1:], ref[:, 1:], 2e-5, "headline form g, sampled leaves")
+
+
+# ------------------------------------------------------- grid model of G_*
+def test_grid_model_forward_matches_oracle_element_by_element(B):
+    N, L, p = 32, 3, 4
+    rho = inputs.lognormal(N, sigma=0.5, seed=77)
+    n = olearn.grid_size(L, p)
+    theta = np.random.default_rng(3).normal(0.0, 0.5, n).astype(np.float32).astype(np.float64)
+    plan = B.Plan(N, L, p)
+    assert B.fmm_plan_table_grid_size(plan.handle) == n
+    B.fmm_plan_set_table_grid(plan.handle, torch.from_numpy(theta.astype(np.float32)).cuda())
+    phi, acc = plan.solve(torch.from_numpy(rho).cuda())
+    torch.cuda.synchronize()
+    plan.close()
+    ophi, og = ofmm.solve(rho, L, p, correction=olearn.grid_correction_fn(theta))
+    plain_phi, _ = ofmm.solve(rho, L, p)
+    assert np.linalg.norm(plain_phi - ophi) > 1e-4 * np.linalg.norm(ophi)
+    assert_close(phi.cpu().numpy(), ophi, 1e-6, "grid model phi")
+    assert_close(acc.cpu().numpy(), og, 1e-6, "grid model g")
+
+
+def test_grid_model_gradient_matches_oracle_finite_differences(B):
+    N, L, p = 16, 3, 2
+    rho = inputs.lognormal(N, sigma=0.8, seed=22)
+    n = olearn.grid_size(L, p)
+    theta = np.random.default_rng(4).normal(0.0, 0.2, n).astype(np.float32).astype(np.float64)
+    tphi, tg = olearn.pm_target(rho)
+    w_phi, w_g = 1.0 / np.sum(tphi ** 2), 1.0 / np.sum(tg ** 2)
+    plan = B.Plan(N, L, p)
+    B.fmm_plan_set_table_grid(plan.handle, torch.from_numpy(theta.astype(np.float32)).cuda())
+    d = torch.from_numpy(rho).cuda()
+    tp = torch.from_numpy(tphi.astype(np.float32)).cuda()
+    ta = torch.from_numpy(tg.astype(np.float32)).contiguous().cuda()
+    grad = torch.zeros(n, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    B.fmm_table_grid_grad(plan.handle, d, tp, ta, w_phi, w_g, grad, loss)
+    torch.cuda.synchronize()
+    g_gpu = grad.cpu().numpy().astype(np.float64)
+    plan.close()
+    j = olearn.grid_loss(theta, rho, L, p, tphi, tg, w_phi, w_g)
+    assert abs(float(loss.item()) - j) <= 1e-3 * j
+    # entries with the largest gradients on every level and field, plus a few others
+    G3 = (4 * p) ** 3
+    idx = []
+    for lev in range(L - 1):
+        for f in range(4):
+            blk = slice((lev * 4 + f) * G3, (lev * 4 + f + 1) * G3)
+            idx.append(blk.start + int(np.argmax(np.abs(g_gpu[blk]))))
+    idx += [5, n // 2 + 3]
+    for i in idx:
+        h = 1e-3
+        tp_, tm_ = theta.copy(), theta.copy()
+        tp_[i] += h
+        tm_[i] -= h
+        fd = (olearn.grid_loss(tp_, rho, L, p, tphi, tg, w_phi, w_g)
+              - olearn.grid_loss(tm_, rho, L, p, tphi, tg, w_phi, w_g)) / (2 * h)
+        scale = max(abs(fd), 1e-3 * np.abs(g_gpu).max())
+        assert abs(g_gpu[i] - fd) <= 2e-2 * scale, (i, g_gpu[i], fd)
+
+
+def test_grid_model_training_gains_on_held_out_fields(B):
+    # Sec. 4's grid model trained against PM(G_S1) on seeded fields; its
+    # held-out error is compared with the plain tables (and printed beside the
+    # network's from the same fields and steps)
+    from paper_2011_07099_gb300 import learn
+    N, L, p = 32, 3, 4
+    train_np = [inputs.lognormal(N, sigma=0.5, seed=100 + i) for i in range(8)]
+    held_np = [inputs.lognormal(N, sigma=0.5, seed=900 + i) for i in range(4)]
+    plain = B.Plan(N, L, p)
+    res = {}
+    for model, lr in (("grid", 2e-2), ("mlp", 2e-3)):
+        tr = learn.Trainer(N, L, p, seed=7, lr=lr, model=model)
+        train = [tr.prepare(x) for x in train_np]
+        held = [tr.prepare(x) for x in held_np]
+        before = np.mean([learn.relative_errors(plain, *f[:3]) for f in held], axis=0)
+        losses = [tr.step(train) for _ in range(120)]
+        after = np.mean([learn.relative_errors(tr.plan, *f[:3]) for f in held], axis=0)
+        res[model] = (before, after, losses[0], losses[-1])
+        print(f"{model}: held-out vs PM(G_S1) plain phi {before[0]:.3e} g {before[1]:.3e} -> "
+              f"phi {after[0]:.3e} g {after[1]:.3e}; loss {losses[0]:.3e} -> {losses[-1]:.3e}")
+    before, after, l0, l1 = res["grid"]
+    assert l1 < l0
+    assert after[0] ** 2 + after[1] ** 2 < 0.99 * (before[0] ** 2 + before[1] ** 2)
+    plain.close()

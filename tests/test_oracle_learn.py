@@ -69,7 +69,7 @@ def test_zero_weights_give_the_plain_fmm():
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
-def _brute_corrected(rho, w, S):
+def _brute_corrected(rho, w, S, entry_fn=None):
     """Direct periodic sum of the two-level tree (L = 2, p = S) with the
     corrected kernel written out per cell pair: at level 2 the gridlet points
     are the cell centres (spacing 1/N), so the interaction-zone pairs use
@@ -85,7 +85,8 @@ def _brute_corrected(rho, w, S):
     G = green.g_s1(d / N, self_value=green.self_term(N))
     mdG = -green.grad_g_s1(d / N)                                  # (t, s, 3)
     uniq, inv = np.unique(d.reshape(-1, 3), axis=0, return_inverse=True)
-    corr = learn.table_correction(w, 2, S, uniq)[inv.ravel()].reshape(N ** 3, N ** 3, 4)
+    entry_fn = entry_fn or (lambda n: learn.table_correction(w, 2, S, n))
+    corr = entry_fn(uniq)[inv.ravel()].reshape(N ** 3, N ** 3, 4)
     corr[near] = 0.0
     phi = (G + corr[..., 0]) @ m
     g = np.stack([(mdG[..., c] + corr[..., 1 + c]) @ m for c in range(3)])
@@ -124,3 +125,39 @@ def test_planted_flip_of_r_minus_s_in_the_correction_is_caught():
     bphi, bg = _brute_corrected(rho, w, S)
     assert np.linalg.norm(phi - bphi) / np.linalg.norm(bphi) > 1e-5
     assert np.linalg.norm(g - bg) / np.linalg.norm(bg) > 1e-3
+
+
+@pytest.mark.parametrize("N", [8, 12])
+def test_grid_model_two_level_tree_equals_the_corrected_direct_sum(N):
+    # the same exact case for the grid model of G_* (Sec. 4): every folded
+    # table value its own parameter, added at the cell offset of each
+    # interaction-zone pair
+    S = N // 4
+    rho = inputs.plummer(N, n_clumps=3, seed=N + 1, a_min=0.5, a_max=2.0)
+    theta = np.random.default_rng(N + 1).normal(0.0, 50.0, learn.grid_size(2, S))
+    phi, g = fmm.solve(rho, 2, S, correction=learn.grid_correction_fn(theta))
+    bphi, bg = _brute_corrected(rho, None, S, entry_fn=lambda n: learn.grid_table_correction(theta, 2, S, n))
+    plain_phi, plain_g = fmm.solve(rho, 2, S)
+    assert np.linalg.norm(plain_g - bg) / np.linalg.norm(bg) > 1e-4
+    assert np.linalg.norm(phi - bphi) / np.linalg.norm(bphi) < 1e-12
+    assert np.linalg.norm(g - bg) / np.linalg.norm(bg) < 1e-12
+
+
+def test_grid_model_keeps_parity_and_periodicity():
+    rng = np.random.default_rng(7)
+    p, L = 3, 4
+    theta = rng.normal(0.0, 1.0, learn.grid_size(L, p))
+    for level in (2, 3, 4):
+        n = rng.integers(-(4 * p - 1), 4 * p, (60, 3))
+        c = learn.grid_table_correction(theta, level, p, n)
+        for k in range(3):
+            flip = np.ones(3, dtype=np.int64)
+            flip[k] = -1
+            cf = learn.grid_table_correction(theta, level, p, n * flip)
+            np.testing.assert_array_equal(cf[:, 0], c[:, 0])                 # G even
+            np.testing.assert_array_equal(cf[:, 1 + k], -c[:, 1 + k])        # own gradient odd
+            others = [f for f in (1, 2, 3) if f != 1 + k]
+            np.testing.assert_array_equal(cf[:, others], c[:, others])      # the others even
+        period = 2 ** level * p
+        for e in np.eye(3, dtype=np.int64):
+            np.testing.assert_array_equal(learn.grid_table_correction(theta, level, p, n + period * e), c)
