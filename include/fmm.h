@@ -58,7 +58,8 @@ typedef struct fmm_plan fmm_plan;
 /* ---- plan lifecycle -------------------------------------------------- */
 
 /* Create a plan for an N^3 periodic mesh, leaf level L and gridlet order.
- *   N     mesh cells per dimension; N = S * 2^L with S in {1, 2, 3, 4, 6, 8}.
+ *   N     mesh cells per dimension; N = S * 2^L with S in {1, 2, 3, 4, 6, 8, 16}
+ *         (16 is the sub-grid of the paper's accuracy experiment, Sec. 3).
  *   L     leaf level, 2 <= L <= 8 (L = 2 is the two-level special case of
  *         Sec. 3, exact when order == S; the general case is L >= 3, Sec. 2).
  *   order gridlet points per dimension (N_g), 1 <= order <= 8.
@@ -113,6 +114,38 @@ int fmm_solve_host(fmm_plan* plan, const float* density_host,
  * translation tiles and multipole buffers (synchronous).  Order 1 ignores
  * the tensor-core modes.  FMM_ERR_ARG for an unknown mode. */
 int fmm_plan_set_precision(fmm_plan* plan, int mode);
+
+/* Boundary of the problem.  FMM_BOUNDARY_PERIODIC (default) is the natively
+ * periodic method.  FMM_BOUNDARY_ISOLATED is the non-periodic problem of
+ * Sec. 3's accuracy experiment (eq. gerr), which separates the multipole-
+ * expansion error from the Green's-function error: every table holds the
+ * Newtonian G_0 = -1/(4 pi r) (same cell self term), no mean is removed
+ * (m = rho / N^3), and the interaction and near zones keep only nodes inside
+ * the box (Sec. 2 zones without the wrap).  Corrections (network, grid) and
+ * the G_S ansatz are not applied while isolated.  Re-tabulates
+ * (synchronous).  FMM_ERR_ARG for an unknown value. */
+#define FMM_BOUNDARY_PERIODIC 0
+#define FMM_BOUNDARY_ISOLATED 1
+int fmm_plan_set_boundary(fmm_plan* plan, int boundary);
+
+/* The periodic Green's function of the tables and the near zone.
+ * FMM_GREEN_S1 (default): G_S1 of eq. gfs1.  FMM_GREEN_S: the ansatz G_S of
+ * Sec. 3, xi_n(t) = sin(pi t)/pi + sum_k a_k (sin((2k+1) pi t)/((2k+1) pi)
+ * - sin(pi t)/pi) with a[0..na-1] = a_1..a_na, 1 <= na <= 4 (G_S1 is na = 1,
+ * a_1 = -1/8); used to fit a_k (Table 1).  Corrections (network, grid) apply
+ * to G_S1 only.  Re-tabulates (synchronous).  FMM_ERR_ARG otherwise. */
+#define FMM_GREEN_S1 0
+#define FMM_GREEN_S  1
+int fmm_plan_set_green(fmm_plan* plan, int kind, const double* a, int na);
+
+/* The plan's Green's function sampled on a mesh, for PM references (Sec. 3:
+ * PM and FMM with the same G).  Periodic plans: M = N, entries at offsets
+ * d/N, d in [0, N)^3.  Isolated plans: M = 2N, the zero-padded (Hockney)
+ * mesh, G_0 at signed offsets k/N with k in [-N, N) stored in FFT order
+ * (index k mod 2N).  d = 0 holds the cell self term.  `out` (device,
+ * 4 M^3 doubles, written; evaluated in FP64): G, -dG/dx, -dG/dy, -dG/dz,
+ * each M^3 with x fastest.  Enqueued on `stream`. */
+int fmm_plan_mesh_green(const fmm_plan* plan, double* out, void* stream);
 
 /* Limit of every bounded device-side wait (pipeline barriers of the
  * tensor-core M2L), in milliseconds, 1..600000; default 2000.  A wait that

@@ -235,13 +235,15 @@ def m2l_kernel(level, p, off_zyx):
     return np.concatenate([G[None], -np.moveaxis(dG, -1, 0)], axis=0)
 
 
-def p2p_kernel(N, S, off_zyx):
+def p2p_kernel(N, S, off_zyx, targets=None):
     """Near-zone matrices (4, S^3, S^3) between a target leaf and the source
     leaf at node offset T - S, cells at spacing 1/N; the coincident cell uses
-    the self term."""
+    the self term.  ``targets`` (flat cell indices in the leaf) keeps only
+    those rows."""
     cells = tensor_points(np.arange(S, dtype=np.float64))
+    tcells = cells if targets is None else cells[np.asarray(targets)]
     d = (np.array(off_zyx[::-1], dtype=np.float64)[None, None, :] * S
-         + cells[:, None, :] - cells[None, :, :]) / N
+         + tcells[:, None, :] - cells[None, :, :]) / N
     G = green.g_s1(d, self_value=green.self_term(N))
     dG = green.grad_g_s1(d)
     return np.concatenate([G[None], -np.moveaxis(dG, -1, 0)], axis=0)
@@ -304,22 +306,24 @@ def downward(M, L, p, correction=None):
 
 
 # ------------------------------------------------------------ near field
-def p2p(m, L, leaves):
+def p2p(m, L, leaves, cells=None):
     """a9: near zone by direct summation over the 27 neighbour leaves of each
-    target leaf ((k,3) array) with periodic wrap.  Returns (k, 4, S^3)."""
+    target leaf ((k,3) array) with periodic wrap.  Returns (k, 4, S^3), or
+    (k, 4, len(cells)) for the given flat cell indices of each leaf."""
     N = m.shape[0]
     n = 2 ** L
     S = N // n
     ml = leaves_of(m, L)
     leaves = np.asarray(leaves, dtype=np.int64).reshape(-1, 3)
-    out = np.zeros((leaves.shape[0], FIELDS, S ** 3))
+    nt = S ** 3 if cells is None else len(cells)
+    out = np.zeros((leaves.shape[0], FIELDS, nt))
     offs = sorted({tuple(int(v) for v in min_image(np.subtract((0, 0, 0), s), n))
                    for s in neighbours(L, (0, 0, 0))})
     for off in offs:
-        K = p2p_kernel(N, S, off)
+        K = p2p_kernel(N, S, off, cells)
         src = (leaves - np.array(off)) % n
         ms = ml[src[:, 0], src[:, 1], src[:, 2]]
-        out += (ms @ K.reshape(FIELDS * S ** 3, S ** 3).T).reshape(-1, FIELDS, S ** 3)
+        out += (ms @ K.reshape(FIELDS * nt, S ** 3).T).reshape(-1, FIELDS, nt)
     return out
 
 
@@ -348,11 +352,12 @@ def solve(rho, L, p, correction=None):
     return mesh[0], mesh[1:]
 
 
-def solve_at(rho, L, p, leaves, correction=None):
+def solve_at(rho, L, p, leaves, correction=None, cells=None):
     """The same solve evaluated only in the given leaves ((k,3), (z,y,x)):
     the whole upward pass, then the local fields along each leaf's chain of
     ancestors, L2P and P2P in those leaves.  Returns (k, 4, S^3) with cells
-    flattened x fastest within the leaf.  ``correction`` as in ``m2l``."""
+    flattened x fastest within the leaf, or (k, 4, len(cells)) for the given
+    flat cell indices.  ``correction`` as in ``m2l``."""
     rho = np.asarray(rho, dtype=np.float64)
     N = rho.shape[0]
     S = N // 2 ** L
@@ -368,5 +373,8 @@ def solve_at(rho, L, p, leaves, correction=None):
             for i in range(anc.shape[0]):
                 F[i] += l2l(loc[i], p, (int(c[i, 2]), int(c[i, 1]), int(c[i, 0])))
         loc = F
-    far = loc @ l2p_matrix(S, p).T
-    return far + p2p(m, L, leaves)
+    l2p = l2p_matrix(S, p)
+    if cells is not None:
+        l2p = l2p[np.asarray(cells)]
+    far = loc @ l2p.T
+    return far + p2p(m, L, leaves, cells)

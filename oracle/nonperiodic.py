@@ -189,12 +189,13 @@ def _m2l_kernel_g0(level, p, off_zyx):
     return np.concatenate([G[None], -np.moveaxis(dG, -1, 0)], axis=0)
 
 
-@lru_cache(maxsize=None)
-def _p2p_kernel_g0(N, S, off_zyx):
+def _p2p_kernel_g0(N, S, off_zyx, targets=None):
     """Near-zone matrices (4, S^3, S^3) with G_0 between a target leaf and the
-    source leaf at offset T - S; the coincident cell uses the self term."""
+    source leaf at offset T - S; the coincident cell uses the self term.
+    ``targets`` (flat cell indices in the leaf) keeps only those rows."""
     cells = tensor_points(np.arange(S, dtype=np.float64))
-    d = (np.array(off_zyx[::-1], dtype=np.float64)[None, None, :] * S + cells[:, None, :] - cells[None, :, :]) / N
+    tcells = cells if targets is None else cells[np.asarray(targets)]
+    d = (np.array(off_zyx[::-1], dtype=np.float64)[None, None, :] * S + tcells[:, None, :] - cells[None, :, :]) / N
     G = g0_at(d, green.self_term(N))
     dG = grad_g0(d)
     return np.concatenate([G[None], -np.moveaxis(dG, -1, 0)], axis=0)
@@ -228,15 +229,63 @@ def solve_isolated(rho, L, p):
                         F[cz::2, cy::2, cx::2] += l2l(loc, p, (cx, cy, cz))
         loc = F
     far = loc @ l2p_matrix(S, p).T                                 # (n,n,n,4,S^3)
-    ml = leaves_of(m, L)
-    near = np.zeros((n, n, n, FIELDS, S ** 3))
-    for T in map(tuple, all_nodes(L)):
-        for src in neighbours_np(L, T):
-            off = tuple(int(a - b) for a, b in zip(T, src))
-            K = _p2p_kernel_g0(N, S, off).reshape(FIELDS * S ** 3, S ** 3)
-            near[T] += (K @ ml[src]).reshape(FIELDS, S ** 3)
+    near = _near_isolated(m, L, all_nodes(L)).reshape(n, n, n, FIELDS, S ** 3)
     mesh = mesh_of(np.moveaxis(far + near, 3, 0), S)
     return mesh[0], mesh[1:]
+
+
+def _near_isolated(m, L, leaves, cells=None):
+    """Near zone of the isolated problem for the given leaves ((k, 3),
+    (z, y, x)): direct sums with G_0 over the in-box neighbour leaves, one
+    offset at a time.  Returns (k, 4, S^3) or (k, 4, len(cells))."""
+    N = m.shape[0]
+    n = 2 ** L
+    S = N // n
+    ml = leaves_of(m, L)
+    leaves = np.asarray(leaves, dtype=np.int64).reshape(-1, 3)
+    nt = S ** 3 if cells is None else len(cells)
+    out = np.zeros((leaves.shape[0], FIELDS, nt))
+    for off in [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]:
+        src = leaves - np.array(off)
+        ok = np.all((src >= 0) & (src < n), axis=1)
+        if not ok.any():
+            continue
+        K = _p2p_kernel_g0(N, S, off, cells).reshape(FIELDS * nt, S ** 3)
+        s = src[ok]
+        out[ok] += (ml[s[:, 0], s[:, 1], s[:, 2]] @ K.T).reshape(-1, FIELDS, nt)
+    return out
+
+
+def solve_isolated_at(rho, L, p, leaves, cells=None):
+    """``solve_isolated`` evaluated only in the given leaves ((k, 3), (z, y,
+    x)) and, if given, only at the flat cell indices ``cells`` of each:
+    the whole upward pass, the local fields along each leaf's chain of
+    ancestors (isolated interaction lists), L2P and the isolated near zone."""
+    rho = np.asarray(rho, dtype=np.float64)
+    N = rho.shape[0]
+    S = N // 2 ** L
+    m = masses_isolated(rho)
+    M = upward(m, L, p)
+    P3 = p ** 3
+    leaves = np.asarray(leaves, dtype=np.int64).reshape(-1, 3)
+    loc = None
+    for lev in range(2, L + 1):
+        anc = leaves >> (L - lev)
+        F = np.zeros((len(leaves), FIELDS, P3))
+        for i, T in enumerate(map(tuple, anc)):
+            for src in interaction_list_np(lev, T):
+                off = tuple(int(a - b) for a, b in zip(T, src))
+                K = _m2l_kernel_g0(lev, p, off).reshape(FIELDS * P3, P3)
+                F[i] += (K @ M[lev][src]).reshape(FIELDS, P3)
+        if loc is not None:
+            c = anc % 2
+            for i in range(len(leaves)):
+                F[i] += l2l(loc[i], p, (int(c[i, 2]), int(c[i, 1]), int(c[i, 0])))
+        loc = F
+    l2p = l2p_matrix(S, p)
+    if cells is not None:
+        l2p = l2p[np.asarray(cells)]
+    return loc @ l2p.T + _near_isolated(m, L, leaves, cells)
 
 
 # --------------------------------------------------------------- eq. gerr

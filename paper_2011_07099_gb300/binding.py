@@ -31,6 +31,12 @@ FMM_INFER_FP32 = 1
 FMM_FAULT_NONE = 0
 FMM_FAULT_TC_STALL = 1
 
+FMM_BOUNDARY_PERIODIC = 0
+FMM_BOUNDARY_ISOLATED = 1
+
+FMM_GREEN_S1 = 0
+FMM_GREEN_S = 1
+
 FMM_STAGE_MULTIPOLE = 0
 FMM_STAGE_LOCAL = 1
 FMM_STAGE_MEAN = 2
@@ -57,6 +63,9 @@ SIGNATURES = {
     "fmm_mean_density_noalloc": (_I, [_FP, _SZ, _FP, _VP]),
     "fmm_probe_fma": (_I, [_FP, _I, _I, _VP]),
     "fmm_plan_table_grid_size": (_I, [_VP, ctypes.POINTER(_SZ)]),
+    "fmm_plan_set_boundary": (_I, [_VP, _I]),
+    "fmm_plan_set_green": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_double), _I]),
+    "fmm_plan_mesh_green": (_I, [_VP, _FP, _VP]),
     "fmm_plan_set_table_grid": (_I, [_VP, _FP, _SZ]),
     "fmm_table_grid_grad": (_I, [_VP, _FP, _FP, _FP, ctypes.c_float, ctypes.c_float, _FP, _FP, _VP]),
     "fmm_probe_fma_flops": (ctypes.c_double, [_I, _I]),
@@ -207,6 +216,19 @@ def fmm_adam_step(weights, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-
 
 def fmm_mesh_green(N, out, stream=None):
     _check(lib().fmm_mesh_green(int(N), out.data_ptr(), _stream_of(out, stream)), "fmm_mesh_green")
+
+
+def fmm_plan_set_boundary(plan, boundary):
+    _check(lib().fmm_plan_set_boundary(plan, int(boundary)), "fmm_plan_set_boundary")
+
+
+def fmm_plan_set_green(plan, kind, a=()):
+    arr = (ctypes.c_double * max(1, len(a)))(*[float(x) for x in a])
+    _check(lib().fmm_plan_set_green(plan, int(kind), arr if len(a) else None, len(a)), "fmm_plan_set_green")
+
+
+def fmm_plan_mesh_green(plan, out, stream=None):
+    _check(lib().fmm_plan_mesh_green(plan, out.data_ptr(), _stream_of(out, stream)), "fmm_plan_mesh_green")
 
 
 def fmm_plan_table_grid_size(plan):

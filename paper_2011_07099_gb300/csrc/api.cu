@@ -88,6 +88,27 @@ std::vector<int8_t> interaction_offsets(int level, int c) {
   return out;
 }
 
+// Offsets of the isolated problem's interaction zones at level 2 (Sec. 3's
+// non-periodic reference, Sec. 2 zones without the wrap): the parent level 1
+// has 2 nodes per dimension, all neighbours of each other, so a level-2
+// node's zone is every in-box node that is not its neighbour; as offsets
+// o = T - S, every o in [-3, 3]^3 with max |o_i| >= 2 (316), the in-box test
+// being done by the kernels.  Levels >= 3 use the periodic lists: a periodic
+// list restricted to in-box sources is the isolated list there.
+std::vector<int8_t> isolated_level2_offsets() {
+  std::vector<int8_t> out;
+  for (int z = -3; z <= 3; ++z)
+    for (int y = -3; y <= 3; ++y)
+      for (int x = -3; x <= 3; ++x) {
+        const int m = std::max(std::abs(x), std::max(std::abs(y), std::abs(z)));
+        if (m < 2) continue;
+        out.push_back((int8_t)x);
+        out.push_back((int8_t)y);
+        out.push_back((int8_t)z);
+      }
+  return out;
+}
+
 void free_plan(Plan* P) {
   if (!P) return;
   cudaFree(P->d_partials);
@@ -202,7 +223,7 @@ fmm_plan* fmm_plan_create(int N, int L, int order) {
     return nullptr;
   }
   const int S = N / n;
-  if (S != 1 && S != 2 && S != 3 && S != 4 && S != 6 && S != 8) {
+  if (S != 1 && S != 2 && S != 3 && S != 4 && S != 6 && S != 8 && S != 16) {
     set_err(FMM_ERR_ARG);
     return nullptr;
   }
@@ -360,6 +381,56 @@ int fmm_plan_set_precision(fmm_plan* plan, int mode) {
   return set_err(FMM_OK);
 }
 
+int fmm_plan_set_boundary(fmm_plan* plan, int boundary) {
+  if (!plan || (boundary != FMM_BOUNDARY_PERIODIC && boundary != FMM_BOUNDARY_ISOLATED)) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  const int iso = boundary == FMM_BOUNDARY_ISOLATED ? 1 : 0;
+  if (iso == P.iso) return set_err(FMM_OK);
+  FMM_CUDA_TRY(cudaDeviceSynchronize());
+  // level-2 interaction lists: 37 periodic nodes, or the 316 in-box offsets
+  std::vector<int8_t> all;
+  int count = 0;
+  for (int c = 0; c < 8; ++c) {
+    std::vector<int8_t> o = iso ? isolated_level2_offsets() : interaction_offsets(2, c);
+    count = (int)o.size() / 3;
+    all.insert(all.end(), o.begin(), o.end());
+  }
+  int8_t* offs = nullptr;
+  if (!dev_alloc(&offs, all.size())) return set_err(FMM_ERR_ALLOC);
+  if (cudaMemcpy(offs, all.data(), all.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(offs);
+    return set_err(FMM_ERR_CUDA);
+  }
+  cudaFree(P.offsets[2]);
+  P.offsets[2] = offs;
+  P.n_off[2] = count;
+  P.iso = iso;
+  // the offset-range scratch of the coarse levels follows the list length
+  size_t part = 0;
+  const size_t p3 = (size_t)P.p * P.p * P.p;
+  for (int l = 2; l <= P.L; ++l)
+    if (fmm::wide_level(P, l)) {
+      const size_t need = 2 * (size_t)fmm::m2l_fp32_splits(P, l) * ((size_t)1 << (3 * l)) * 4 * p3;
+      if (need > part) part = need;
+    }
+  cudaFree(P.m2l_part);
+  P.m2l_part = nullptr;
+  if (!dev_alloc(&P.m2l_part, part)) return set_err(FMM_ERR_ALLOC);
+  return set_err(retabulate(P));
+}
+
+int fmm_plan_set_green(fmm_plan* plan, int kind, const double* a, int na) {
+  if (!plan || (kind != FMM_GREEN_S1 && kind != FMM_GREEN_S)) return set_err(FMM_ERR_ARG);
+  if (kind == FMM_GREEN_S && (na < 1 || na > fmm::green::kMaxAnsatz || !a)) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  fmm::green::Spec g;
+  g.kind = kind == FMM_GREEN_S ? 1 : 0;
+  g.na = kind == FMM_GREEN_S ? na : 0;
+  for (int k = 0; k < g.na; ++k) g.a[k] = a[k];
+  P.gspec = g;
+  return set_err(retabulate(P));
+}
+
 int fmm_plan_set_timeout_ms(fmm_plan* plan, int ms) {
   if (!plan || ms < 1 || ms > 600000) return set_err(FMM_ERR_ARG);
   reinterpret_cast<Plan*>(plan)->wait_ns = (uint64_t)ms * 1000000ull;
@@ -468,6 +539,13 @@ int fmm_mesh_green(int N, float* out, void* stream) {
   return set_err(FMM_OK);
 }
 
+int fmm_plan_mesh_green(const fmm_plan* plan, double* out, void* stream) {
+  if (!plan || !out) return set_err(FMM_ERR_ARG);
+  const Plan& P = *reinterpret_cast<const Plan*>(plan);
+  FMM_CUDA_TRY(fmm::launch_mesh_green_plan(P, out, reinterpret_cast<cudaStream_t>(stream)));
+  return set_err(FMM_OK);
+}
+
 int fmm_plan_check(fmm_plan* plan) {
   if (!plan) return set_err(FMM_ERR_ARG);
   Plan& P = *reinterpret_cast<Plan*>(plan);
@@ -517,7 +595,10 @@ int fmm_solve(fmm_plan* plan, const float* density, float* potential, float* acc
     return t ? cudaEventRecord(P.ev[2 * slot + end], s) : cudaSuccess;
   };
   FMM_CUDA_TRY(mark(FMM_TIME_MEAN, 0));
-  FMM_CUDA_TRY(fmm::launch_mean(P, density, s));
+  if (P.iso)   // the isolated problem keeps every mass (m = rho / N^3)
+    FMM_CUDA_TRY(cudaMemsetAsync(P.d_mean, 0, sizeof(double), s));
+  else
+    FMM_CUDA_TRY(fmm::launch_mean(P, density, s));
   FMM_CUDA_TRY(mark(FMM_TIME_MEAN, 1));
   FMM_CUDA_TRY(mark(FMM_TIME_P2M, 0));
   FMM_CUDA_TRY(fmm::launch_p2m(P, density, s));

@@ -6,6 +6,7 @@
 #include <cstddef>
 
 #include "../../include/fmm.h"
+#include "green_s1.cuh"
 
 namespace fmm {
 
@@ -62,6 +63,11 @@ constexpr int kWideOrder = 7;
 struct Plan {
   int N = 0, L = 0, p = 0, S = 0;
   int prec = FMM_PREC_FP32;
+  // the tabulated Green's function (G_S1 by default) and the boundary: in the
+  // isolated problem (iso = 1) every table holds G_0, no mean is removed and
+  // interaction and near zones keep only in-box nodes
+  green::Spec gspec;
+  int iso = 0;
   int device = 0;
   int num_sms = 0;
   int solved = 0;
@@ -164,6 +170,7 @@ int mlp_backward_blocks(const Plan& P);
 cudaError_t launch_adam(float* w, const float* g, float* m, float* v, size_t n, int step, float lr, float b1, float b2,
                         float eps, cudaStream_t s);
 cudaError_t launch_mesh_green(int N, float* out, int sms, cudaStream_t s);
+cudaError_t launch_mesh_green_plan(const Plan& P, double* out, cudaStream_t s);
 // Sampled error against the direct periodic sum with G_S1 (errstats.cu):
 // targets T <= error_stats_max_samples(), partials error_stats_grid_x(P, T)
 // x T x 4 doubles, sums 4 doubles, mean_scratch P.n_partials + 1 doubles

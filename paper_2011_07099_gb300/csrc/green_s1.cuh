@@ -1,18 +1,34 @@
-// G_S1, the approximately optimal periodic Green's function (Sec. 3, n = 1,
-// a_1 = -1/8), in FP64 for the table and mesh kernels.
+// Green's functions of the tables, in FP64 for the table and mesh kernels.
 //
+// G_S1, the approximately optimal periodic Green's function (Sec. 3, n = 1,
+// a_1 = -1/8; eq. gfs1):
 //   G(x) = -1/(4 pi |xhat|),  xhat_i = xi(x_i),
 //   xi(t) = (9/(8 pi)) sin(pi t) - (1/(24 pi)) sin(3 pi t).
-//
 // xi is odd-periodic, so |xhat| and G are 1-periodic and the wrap of xhat is a
 // no-op.  Gradient by the chain rule: dG/dx_i = xhat_i xi'(x_i) / (4 pi
 // |xhat|^3), xi'(t) = (9/8) cos(pi t) - (1/8) cos(3 pi t).
+//
+// G_S, the ansatz of Sec. 3 with free coefficients a_1..a_n:
+//   xi_n(t) = sin(pi t)/pi + sum_k a_k (sin((2k+1) pi t)/((2k+1) pi) - sin(pi t)/pi),
+// G_S1 being n = 1, a_1 = -1/8.
+//
+// G_0 = -1/(4 pi r), the Newtonian Green's function of the isolated
+// (non-periodic) problem of Sec. 3's accuracy experiment (eq. gerr).
 #pragma once
 
 namespace fmm {
 namespace green {
 
 constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxAnsatz = 4;     // coefficients a_1..a_4 of the G_S ansatz
+
+// Which function a plan tabulates (FMM_GREEN_* of fmm.h), with the ansatz
+// coefficients of G_S.
+struct Spec {
+  int kind = 0;                   // 0 G_S1, 1 G_S(a), 2 G_0
+  int na = 0;
+  double a[kMaxAnsatz] = {0.0, 0.0, 0.0, 0.0};
+};
 
 // Mean of 1/r over the unit cube: 3 ln(2 + sqrt 3) - pi/2.  The paper does not
 // define the self term G(0); the cell-averaged Newtonian value is used.
@@ -34,6 +50,54 @@ __device__ inline void gs1(double x, double y, double z, double out[4]) {
   out[1] = c * hx * dxi_s1(x);
   out[2] = c * hy * dxi_s1(y);
   out[3] = c * hz * dxi_s1(z);
+}
+
+// xi_n of the ansatz and its derivative.
+__device__ inline void xi_ansatz(double t, const Spec& g, double& xi, double& dxi) {
+  const double s1 = sinpi(t) / kPi, c1 = cospi(t);
+  xi = s1;
+  dxi = c1;
+  for (int k = 1; k <= g.na; ++k) {
+    const double m = 2.0 * k + 1.0;
+    xi += g.a[k - 1] * (sinpi(m * t) / (m * kPi) - s1);
+    dxi += g.a[k - 1] * (cospi(m * t) - c1);
+  }
+}
+
+// The same four values for G_S(a) (periodic, like G_S1).
+__device__ inline void gs_ansatz(double x, double y, double z, const Spec& g, double out[4]) {
+  double h[3], d[3];
+  xi_ansatz(x, g, h[0], d[0]);
+  xi_ansatz(y, g, h[1], d[1]);
+  xi_ansatz(z, g, h[2], d[2]);
+  const double r2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
+  const double r = sqrt(r2);
+  const double inv4pi = 1.0 / (4.0 * kPi);
+  out[0] = -inv4pi / r;
+  const double c = -inv4pi / (r2 * r);
+  for (int i = 0; i < 3; ++i) out[1 + i] = c * h[i] * d[i];
+}
+
+// The same four values for G_0 (no wrap: x is the displacement itself).
+__device__ inline void g0(double x, double y, double z, double out[4]) {
+  const double r2 = x * x + y * y + z * z;
+  const double r = sqrt(r2);
+  const double inv4pi = 1.0 / (4.0 * kPi);
+  out[0] = -inv4pi / r;
+  const double c = -inv4pi / (r2 * r);
+  out[1] = c * x;
+  out[2] = c * y;
+  out[3] = c * z;
+}
+
+// Dispatch on the plan's function; x != 0.
+__device__ inline void eval(const Spec& g, double x, double y, double z, double out[4]) {
+  if (g.kind == 1)
+    gs_ansatz(x, y, z, g, out);
+  else if (g.kind == 2)
+    g0(x, y, z, out);
+  else
+    gs1(x, y, z, out);
 }
 
 }  // namespace green

@@ -348,7 +348,38 @@ __global__ void k_mesh_green(int N, float* __restrict__ out) {
   }
 }
 
+// The plan's Green's function on a mesh, for the PM references of Sec. 3:
+// periodic (M = N): offsets d/N, d in [0, N)^3, the function the plan
+// tabulates; isolated (M = 2N, the zero-padded Hockney mesh): G_0 at signed
+// offsets k/N, k in [-N, N) in FFT order.  Self term at d = 0.
+__global__ void k_mesh_green_plan(int N, int M, green::Spec gs, double* __restrict__ out) {
+  const size_t m3 = (size_t)M * M * M;
+  const double inv4pi = 1.0 / (4.0 * green::kPi);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m3; i += (size_t)gridDim.x * blockDim.x) {
+    int k[3] = {(int)(i % M), (int)((i / M) % M), (int)(i / ((size_t)M * M))};
+    if (M != N)
+      for (int c = 0; c < 3; ++c)
+        if (k[c] >= N) k[c] -= M;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (k[0] | k[1] | k[2])
+      green::eval(gs, (double)k[0] / N, (double)k[1] / N, (double)k[2] / N, v);
+    else
+      v[0] = -green::cube_mean_inv_r() * N * inv4pi;
+    for (int f = 0; f < 4; ++f) out[f * m3 + i] = v[f];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_mesh_green_plan(const Plan& P, double* out, cudaStream_t s) {
+  green::Spec g = P.gspec;
+  if (P.iso) {
+    g = green::Spec();
+    g.kind = 2;
+  }
+  k_mesh_green_plan<<<4 * P.num_sms, 256, 0, s>>>(P.N, P.iso ? 2 * P.N : P.N, g, out);
+  return cudaGetLastError();
+}
 
 // --------------------------------------------------------------- launchers
 cudaError_t launch_residual(const float* phi, const float* acc, const float* tphi, const float* tacc, size_t n3,

@@ -50,7 +50,7 @@ template <int P, int EXT>
 __global__ void __launch_bounds__(M2LShape<P>::THREADS)
 k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __restrict__ tab,
            const float4* __restrict__ tab_lo, const int8_t* __restrict__ offs, int n_off, int level,
-           int per_split, size_t split_stride, int pairs, const double* __restrict__ M64) {
+           int per_split, size_t split_stride, int pairs, const double* __restrict__ M64, int iso) {
   constexpr int P3 = P * P * P;
   constexpr int NT = M2LShape<P>::NT;
   constexpr int D = 2 * P - 1;          // table window per dimension
@@ -107,9 +107,12 @@ k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __r
     for (int i = tid; i < NT * P3; i += nthr) {
       const int k = i / P3, s = i % P3;
       float v = 0.f, vlo = 0.f;
-      if (par0 + k < n_par) {
-        const uint32_t sx = (uint32_t)(tx[k] - ox) & (n - 1), sy = (uint32_t)(ty[k] - oy) & (n - 1),
-                       sz = (uint32_t)(tz[k] - oz) & (n - 1);
+      // the source node T - o, wrapped (periodic) or, in the isolated
+      // problem, skipped when it lies outside the box
+      const int ux = tx[k] - ox, uy = ty[k] - oy, uz = tz[k] - oz;
+      const bool inbox = (unsigned)ux < (unsigned)n && (unsigned)uy < (unsigned)n && (unsigned)uz < (unsigned)n;
+      if (par0 + k < n_par && (inbox || !iso)) {
+        const uint32_t sx = (uint32_t)ux & (n - 1), sy = (uint32_t)uy & (n - 1), sz = (uint32_t)uz & (n - 1);
         const size_t g = (size_t)morton(sx, sy, sz) * P3 + s;
         if (EXT == 3) {
           const double d = __ldg(M64 + g);
@@ -237,7 +240,7 @@ template <int P>
 __global__ void __launch_bounds__(M2LShape<P>::THREADS, P >= kWideOrder ? 1 : 2)
 k_m2l_df(const float* __restrict__ M, float* __restrict__ F, const float4* __restrict__ tab,
          const float4* __restrict__ tab_lo, const int8_t* __restrict__ offs, int n_off, int level, int per_split,
-         size_t split_stride, int pairs, const double* __restrict__ M64) {
+         size_t split_stride, int pairs, const double* __restrict__ M64, int iso) {
   constexpr int P3 = P * P * P;
   constexpr int NT = M2LShape<P>::NT;
   constexpr int D = 2 * P - 1;
@@ -289,9 +292,12 @@ k_m2l_df(const float* __restrict__ M, float* __restrict__ F, const float4* __res
     for (int i = tid; i < NT * P3; i += nthr) {
       const int k = i / P3, s = i % P3;
       float v = 0.f, vlo = 0.f;
-      if (par0 + k < n_par) {
-        const uint32_t sx = (uint32_t)(tx[k] - ox) & (n - 1), sy = (uint32_t)(ty[k] - oy) & (n - 1),
-                       sz = (uint32_t)(tz[k] - oz) & (n - 1);
+      // the source node T - o, wrapped (periodic) or, in the isolated
+      // problem, skipped when it lies outside the box
+      const int ux = tx[k] - ox, uy = ty[k] - oy, uz = tz[k] - oz;
+      const bool inbox = (unsigned)ux < (unsigned)n && (unsigned)uy < (unsigned)n && (unsigned)uz < (unsigned)n;
+      if (par0 + k < n_par && (inbox || !iso)) {
+        const uint32_t sx = (uint32_t)ux & (n - 1), sy = (uint32_t)uy & (n - 1), sz = (uint32_t)uz & (n - 1);
         const size_t g = (size_t)morton(sx, sy, sz) * P3 + s;
         if (M64) {
           const double d = __ldg(M64 + g);
@@ -395,16 +401,19 @@ cudaError_t launch_p(Plan& Pl, int level, cudaStream_t s) {
   const double* m64 = wide ? Pl.M64[level] : nullptr;   // FP64 masses: wide levels of the high orders
   if (level == 2 || m64)   // double-float sums: level 2, and every wide level of the high orders
     k_m2l_df<P><<<grid, threads, sizeof(float4) * (2 * D * D * D + 2 * P3 * (NT / 4)), s>>>(
-        Pl.M[level], out, Pl.tab[level], Pl.tab_lo[level], Pl.offsets[level], n_off, level, per, field, 1, m64);
+        Pl.M[level], out, Pl.tab[level], Pl.tab_lo[level], Pl.offsets[level], n_off, level, per, field, 1, m64,
+        Pl.iso);
   else if (m64)
     k_m2l_fp32<P, 3><<<grid, threads, sizeof(float4) * (2 * D * D * D + 2 * P3 * (NT / 4)), s>>>(
-        Pl.M[level], out, Pl.tab[level], Pl.tab_lo[level], Pl.offsets[level], n_off, level, per, field, 1, m64);
+        Pl.M[level], out, Pl.tab[level], Pl.tab_lo[level], Pl.offsets[level], n_off, level, per, field, 1, m64,
+        Pl.iso);
   else if (ext)
     k_m2l_fp32<P, EXT_TOP><<<grid, threads, smem, s>>>(Pl.M[level], out, Pl.tab[level], Pl.tab_lo[level],
-                                                       Pl.offsets[level], n_off, level, per, field, 1, nullptr);
+                                                       Pl.offsets[level], n_off, level, per, field, 1, nullptr,
+                                                       Pl.iso);
   else
     k_m2l_fp32<P, 0><<<grid, threads, smem, s>>>(Pl.M[level], out, Pl.tab[level], nullptr, Pl.offsets[level],
-                                                 n_off, level, per, field, wide ? 1 : 0, nullptr);
+                                                 n_off, level, per, field, wide ? 1 : 0, nullptr, Pl.iso);
   if (wide) k_sum_ranges<<<4 * Pl.num_sms, 256, 0, s>>>(Pl.m2l_part, nsplit, field, Pl.F64[level], Pl.F[level]);
   return cudaGetLastError();
 }

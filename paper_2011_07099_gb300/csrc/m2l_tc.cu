@@ -77,7 +77,7 @@ template <int P, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre,
          const int8_t* __restrict__ offs, int n_off, int level, int group,
-         float* __restrict__ F, int* __restrict__ err, uint64_t kWaitNs, int stall) {
+         float* __restrict__ F, int* __restrict__ err, uint64_t kWaitNs, int stall, int iso) {
   using Sh = TcShape<P, MODE>;
   constexpr int P3 = Sh::P3, KP = Sh::KP, NCH = Sh::NCH, MT = Sh::MT, ST = Sh::ST, NSPLIT = Sh::NSPLIT;
   constexpr int STAGE_BYTES = Sh::STAGE_BYTES;
@@ -191,7 +191,11 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
         if (par0 + pt < n_par) {
           uint32_t x, y, z;
           unmorton(8u * (par0 + pt) + ctype, x, y, z);
-          key = (int)morton((x - ox) & (n - 1), (y - oy) & (n - 1), (z - oz) & (n - 1));
+          // the source node, wrapped; in the isolated problem a source
+          // outside the box contributes nothing (zero-filled like padding)
+          const int ux = (int)x - ox, uy = (int)y - oy, uz = (int)z - oz;
+          const bool inbox = (unsigned)ux < (unsigned)n && (unsigned)uy < (unsigned)n && (unsigned)uz < (unsigned)n;
+          if (inbox || !iso) key = (int)morton((uint32_t)ux & (n - 1), (uint32_t)uy & (n - 1), (uint32_t)uz & (n - 1));
         }
         srckey[b * kNT + pt] = key;
       }
@@ -369,7 +373,7 @@ cudaError_t launch_one(Plan& Pl, int level, cudaStream_t s) {
   const uint8_t* Apre = static_cast<const uint8_t*>(Pl.Apre[level]);
   k_m2l_tc<P, MODE><<<grid, kThreads, smem_bytes<P, MODE>(), s>>>(
       Msp, Apre, Pl.offsets[level], Pl.n_off[level], level, Pl.tc_group, Pl.F[level], Pl.d_err, Pl.wait_ns,
-      Pl.inject_stall);
+      Pl.inject_stall, Pl.iso);
   return cudaGetLastError();
 }
 

@@ -65,7 +65,7 @@ template <int S>
 __global__ void __launch_bounds__(P2PShape<S>::THREADS, 1)
 k_p2p(const float* __restrict__ rho, const double* __restrict__ mean, int N, int L, int p,
       const float4* __restrict__ near_tab, const float* __restrict__ Fleaf, const float2* __restrict__ wp2m,
-      float* __restrict__ phi, float* __restrict__ acc_out, int vec) {
+      float* __restrict__ phi, float* __restrict__ acc_out, int vec, int iso) {
   using Sh = P2PShape<S>;
   constexpr int W = Sh::W, TD = Sh::TD, TS = Sh::TS, ROWS = Sh::ROWS, NZG = Sh::NZG;
   extern __shared__ float4 sm4[];
@@ -101,14 +101,20 @@ k_p2p(const float* __restrict__ rho, const double* __restrict__ mean, int N, int
       constexpr int C = S % 4 == 0 ? W / 4 : 1;
       for (int i = tid; i < W * W * C; i += nthr) {
         const int c = i % C, wy = (i / C) % W, wz = i / (C * W);
-        const int gx = (x0 + 4 * c + N) % N, gy = (y0 + wy + N) % N, gz = (z0 + wz + N) % N;
-        tc::cp_async16(tc::smem_u32(win + (wz * W + wy) * W + 4 * c), rho + ((size_t)gz * N + gy) * N + gx, 16u);
+        const int ux = x0 + 4 * c, uy = y0 + wy, uz = z0 + wz;
+        const int gx = (ux + N) % N, gy = (uy + N) % N, gz = (uz + N) % N;
+        // isolated problem: cells outside the box hold no mass (zero fill)
+        const bool out = iso && (gx != ux || gy != uy || gz != uz);
+        tc::cp_async16(tc::smem_u32(win + (wz * W + wy) * W + 4 * c), rho + ((size_t)gz * N + gy) * N + gx,
+                       out ? 0u : 16u);
       }
     } else {
       for (int i = tid; i < W * W * W; i += nthr) {
         const int wx = i % W, wy = (i / W) % W, wz = i / (W * W);
-        const int gx = (x0 + wx + N) % N, gy = (y0 + wy + N) % N, gz = (z0 + wz + N) % N;
-        tc::cp_async4(tc::smem_u32(win + i), rho + ((size_t)gz * N + gy) * N + gx);
+        const int ux = x0 + wx, uy = y0 + wy, uz = z0 + wz;
+        const int gx = (ux + N) % N, gy = (uy + N) % N, gz = (uz + N) % N;
+        const bool out = iso && (gx != ux || gy != uy || gz != uz);
+        tc::cp_async4_zfill(tc::smem_u32(win + i), rho + ((size_t)gz * N + gy) * N + gx, out ? 0u : 4u);
       }
     }
     const float* src = Fleaf + (size_t)leaf * 4 * p3;
@@ -227,6 +233,195 @@ k_p2p(const float* __restrict__ rho, const double* __restrict__ mean, int N, int
   }
 }
 
+// Leaf size 16, the sub-grid of the paper's accuracy experiment (Sec. 3:
+// 16^3 cells per node, significantly more than the gridlet).  The 48^3 window
+// and the 32^3 folded table do not fit in shared memory, so the window is
+// streamed one source plane at a time (cp.async double buffer) and the table
+// is read through the L1 cache.  Two CTAs per leaf (target planes 0-7 and
+// 8-15) of 256 threads: thread (cz, cy, h) owns the 8 cells x in [8h, 8h + 8)
+// of target row (cz, cy), 4 fields.  A source row's 48 cells are taken 8 at a
+// time: for chunk c the offsets dx = 8 (2 + h - c) + (x - xs) span 15
+// consecutive values, whose table entries are loaded into registers once per
+// chunk; the sign of dx is the same for the whole chunk except in the
+// target's own chunk (base 0), where it is resolved at compile time.  The
+// summation keeps the row -> plane -> total partial sums of the kernel above.
+constexpr int kS16 = 16, kW16 = 48, kT16 = 256;
+
+struct P2P16Smem {
+  int far, w8, t1, t2, in, pl0, pl1, total;   // offsets in floats
+  __host__ __device__ P2P16Smem(int p) {
+    far = 0;
+    w8 = 4 * kS16 * kS16 * kS16;
+    t1 = w8 + 2 * p * kS16;
+    t2 = t1 + 4 * p * p * kS16;
+    in = (t2 + 4 * p * kS16 * kS16 + 3) / 4 * 4;
+    pl0 = in + 4 * p * p * p;
+    pl1 = pl0 + kW16 * kW16;
+    total = pl1 + kW16 * kW16;
+  }
+};
+
+template <int SGN>   // +1: every dx > 0, -1: every dx < 0, 0: dx = x - xs
+__device__ __forceinline__ void p2p16_chunk(float rw[4][8], const float4 t[15], const float m[8]) {
+#pragma unroll
+  for (int xs = 0; xs < 8; ++xs) {
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      const float4 v = t[x - xs + 7];
+      rw[0][x] = fmaf(v.x, m[xs], rw[0][x]);
+      const bool neg = SGN < 0 || (SGN == 0 && x < xs);
+      rw[1][x] = neg ? fmaf(-v.y, m[xs], rw[1][x]) : fmaf(v.y, m[xs], rw[1][x]);
+      rw[2][x] = fmaf(v.z, m[xs], rw[2][x]);
+      rw[3][x] = fmaf(v.w, m[xs], rw[3][x]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kT16, 1)
+k_p2p16(const float* __restrict__ rho, const double* __restrict__ mean, int N, int L, int p,
+        const float4* __restrict__ near_tab, const float* __restrict__ Fleaf, const float2* __restrict__ wp2m,
+        float* __restrict__ phi, float* __restrict__ acc_out, int vec, int iso) {
+  extern __shared__ float4 sm4[];
+  float* base = reinterpret_cast<float*>(sm4);
+  const P2P16Smem lay(p);
+  float* far = base + lay.far;
+  float2* W8 = reinterpret_cast<float2*>(base + lay.w8);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int p3 = p * p * p;
+  const unsigned leaf = blockIdx.x >> 1;
+  const int zh = blockIdx.x & 1;
+  const size_t N3 = (size_t)N * N * N;
+  uint32_t lx, ly, lz;
+  unmorton(leaf, lx, ly, lz);
+  const int x0 = (int)lx * kS16 - kS16, y0 = (int)ly * kS16 - kS16, z0 = (int)lz * kS16 - kS16;
+  const double mu = *mean;
+  const float mu_hi = (float)mu, mu_lo = (float)(mu - (double)mu_hi);
+  const float inv_vol = (float)(1.0 / ((double)N * N * N));
+
+  // cp.async of source plane zp of the window (periodic wrap; zero fill
+  // outside the box in the isolated problem) into plane buffer b
+  auto fetch = [&](int zp, int b) {
+    float* pln = base + (b ? lay.pl1 : lay.pl0);
+    const int uz = z0 + zp, gz = (uz + N) % N;
+    const bool outz = iso && gz != uz;
+    if (vec) {
+      for (int i = tid; i < kW16 * (kW16 / 4); i += nthr) {
+        const int c = i % (kW16 / 4), wy = i / (kW16 / 4);
+        const int ux = x0 + 4 * c, uy = y0 + wy;
+        const int gx = (ux + N) % N, gy = (uy + N) % N;
+        const bool out = outz || (iso && (gx != ux || gy != uy));
+        tc::cp_async16(tc::smem_u32(pln + wy * kW16 + 4 * c), rho + ((size_t)gz * N + gy) * N + gx, out ? 0u : 16u);
+      }
+    } else {
+      for (int i = tid; i < kW16 * kW16; i += nthr) {
+        const int wx = i % kW16, wy = i / kW16;
+        const int ux = x0 + wx, uy = y0 + wy;
+        const int gx = (ux + N) % N, gy = (uy + N) % N;
+        const bool out = outz || (iso && (gx != ux || gy != uy));
+        tc::cp_async4_zfill(tc::smem_u32(pln + i), rho + ((size_t)gz * N + gy) * N + gx, out ? 0u : 4u);
+      }
+    }
+    tc::cp_async_commit();
+  };
+
+  fetch(0, 0);
+  for (int i = tid; i < p * kS16; i += nthr) W8[i] = wp2m[i];
+  for (int i = tid; i < 4 * p3; i += nthr) base[lay.in + i] = Fleaf[(size_t)leaf * 4 * p3 + i];
+  __syncthreads();
+  // L2P of the whole leaf (ends with a barrier)
+  contract3(base + lay.in, base + lay.t1, base + lay.t2, far, 4, p, kS16, W8, kS16, true, tid, nthr);
+
+  const int row = tid & 127, h = tid >> 7;
+  const int cz = zh * 8 + (row >> 4), cy = row & 15;
+  float a[4][8];
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int x = 0; x < 8; ++x) a[f][x] = 0.f;
+
+  for (int zp = 0; zp < kW16; ++zp) {
+    float* pln = base + ((zp & 1) ? lay.pl1 : lay.pl0);
+    tc::cp_async_wait<0>();
+    __syncthreads();   // plane zp landed; plane zp - 1 is no longer read
+    for (int i = tid; i < kW16 * kW16; i += nthr) pln[i] = ((pln[i] - mu_hi) - mu_lo) * inv_vol;
+    __syncthreads();
+    if (zp + 1 < kW16) fetch(zp + 1, (zp + 1) & 1);
+    const int dz = cz + kS16 - zp;
+    const int adz = dz < 0 ? -dz : dz;
+    const float sz = dz > 0 ? 1.f : (dz < 0 ? -1.f : 0.f);
+    float pl[4][8];
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int x = 0; x < 8; ++x) pl[f][x] = 0.f;
+#pragma unroll 1
+    for (int yp = 0; yp < kW16; ++yp) {
+      const int dy = cy + kS16 - yp;
+      const int ady = dy < 0 ? -dy : dy;
+      const float sy = dy > 0 ? 1.f : (dy < 0 ? -1.f : 0.f);
+      const float4* trow = near_tab + ((size_t)adz * 2 * kS16 + ady) * 2 * kS16;
+      const float* mrow = pln + yp * kW16;
+      float rw[4][8];
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int x = 0; x < 8; ++x) rw[f][x] = 0.f;
+#pragma unroll 1
+      for (int c = 0; c < kW16 / 8; ++c) {
+        const int b8 = 8 * (2 + h - c);       // dx = b8 + x - xs
+        float4 t[15];
+#pragma unroll
+        for (int j = 0; j < 15; ++j) {
+          const int d = b8 + j - 7;
+          t[j] = __ldg(trow + (d < 0 ? -d : d));
+        }
+        const float4 m0 = *reinterpret_cast<const float4*>(mrow + 8 * c);
+        const float4 m1 = *reinterpret_cast<const float4*>(mrow + 8 * c + 4);
+        const float m[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+        if (b8 > 0)
+          p2p16_chunk<1>(rw, t, m);
+        else if (b8 < 0)
+          p2p16_chunk<-1>(rw, t, m);
+        else
+          p2p16_chunk<0>(rw, t, m);
+      }
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        pl[0][x] += rw[0][x];
+        pl[1][x] += rw[1][x];
+        pl[2][x] = fmaf(sy, rw[2][x], pl[2][x]);
+        pl[3][x] += rw[3][x];
+      }
+    }
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      a[0][x] += pl[0][x];
+      a[1][x] += pl[1][x];
+      a[2][x] += pl[2][x];
+      a[3][x] = fmaf(sz, pl[3][x], a[3][x]);
+    }
+  }
+  const size_t o = ((size_t)(lz * kS16 + cz) * N + (ly * kS16 + cy)) * N + lx * kS16 + 8 * h;
+#pragma unroll
+  for (int x = 0; x < 8; ++x) {
+    const int c = (cz * kS16 + cy) * kS16 + 8 * h + x;
+    const int S3 = kS16 * kS16 * kS16;
+    phi[o + x] = a[0][x] + far[c];
+    acc_out[o + x] = a[1][x] + far[S3 + c];
+    acc_out[N3 + o + x] = a[2][x] + far[2 * S3 + c];
+    acc_out[2 * N3 + o + x] = a[3][x] + far[3 * S3 + c];
+  }
+}
+
+cudaError_t launch_s16(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s) {
+  const size_t smem = sizeof(float) * (size_t)P2P16Smem(P.p).total;
+  const unsigned leaves = 1u << (3 * P.L);
+  const int vec = (reinterpret_cast<uintptr_t>(rho) & 15u) == 0;
+  k_p2p16<<<2 * leaves, kT16, smem, s>>>(rho, P.d_mean, P.N, P.L, P.p, P.near_tab, P.F[P.L], P.w_p2m, phi, acc, vec,
+                                        P.iso);
+  return cudaGetLastError();
+}
+
 template <int S>
 size_t smem_s(int p) {
   using Sh = P2PShape<S>;
@@ -245,7 +440,8 @@ cudaError_t launch_s(Plan& P, const float* rho, float* phi, float* acc, cudaStre
   const unsigned slots = (unsigned)(per_sm * P.num_sms);
   const unsigned grid = leaves < slots ? leaves : slots;
   const int vec = (S % 4 == 0) && ((reinterpret_cast<uintptr_t>(rho) & 15u) == 0);
-  k_p2p<S><<<grid, Sh::THREADS, smem, s>>>(rho, P.d_mean, P.N, P.L, P.p, P.near_tab, P.F[P.L], P.w_p2m, phi, acc, vec);
+  k_p2p<S><<<grid, Sh::THREADS, smem, s>>>(rho, P.d_mean, P.N, P.L, P.p, P.near_tab, P.F[P.L], P.w_p2m, phi, acc, vec,
+                                           P.iso);
   return cudaGetLastError();
 }
 
@@ -264,6 +460,7 @@ cudaError_t setup_p2p(const Plan& P) {
     case 4: return setup_s<4>();
     case 6: return setup_s<6>();
     case 8: return setup_s<8>();
+    case 16: return cudaFuncSetAttribute(k_p2p16, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -276,6 +473,7 @@ cudaError_t launch_p2p(Plan& P, const float* rho, float* phi, float* acc, cudaSt
     case 4: return launch_s<4>(P, rho, phi, acc, s);
     case 6: return launch_s<6>(P, rho, phi, acc, s);
     case 8: return launch_s<8>(P, rho, phi, acc, s);
+    case 16: return launch_s16(P, rho, phi, acc, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -12,7 +12,6 @@ namespace fmm {
 namespace {
 
 using green::cube_mean_inv_r;
-using green::gs1;
 using green::kPi;
 
 // Learned correction of one table entry (all four fields), if weights are set.
@@ -57,14 +56,14 @@ __device__ inline void add_grid(double v[4], int ix, int iy, int iz, int level, 
 // folded over the sign of each component).  Entry n = 0 is never used by M2L
 // (the interaction zone excludes near nodes) and is stored as 0.
 __global__ void k_tab_m2l(float4* __restrict__ out, float4* __restrict__ lo, int p, int level, const float* mlp,
-                          int fp32, const float* grid) {
+                          int fp32, const float* grid, green::Spec gs) {
   const int hw = 4 * p - 1, E = 8 * p - 1;
   const long total = (long)E * E * E;
   const double dx = 1.0 / ((double)(1 << level) * p);
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     const int ix = (int)(i % E) - hw, iy = (int)((i / E) % E) - hw, iz = (int)(i / ((long)E * E)) - hw;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-    if (ix | iy | iz) gs1(ix * dx, iy * dx, iz * dx, v);
+    if (ix | iy | iz) green::eval(gs, ix * dx, iy * dx, iz * dx, v);
     add_correction(v, ix, iy, iz, level, p, mlp, fp32);
     add_grid(v, ix, iy, iz, level, p, grid);
     out[i] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
@@ -79,7 +78,7 @@ __global__ void k_tab_m2l(float4* __restrict__ out, float4* __restrict__ lo, int
 // folded: G is even in every component, -dG/dx_i is odd in x_i and even in the
 // others, so entries hold the values at (|dx|, |dy|, |dz|) and the kernel
 // restores the signs.  d = 0 holds the self term -(1/4 pi) <1/r>_cell / h.
-__global__ void k_tab_near(float4* __restrict__ out, int S, int N) {
+__global__ void k_tab_near(float4* __restrict__ out, int S, int N, green::Spec gs) {
   const int D = 2 * S;
   const int total = D * D * D;
   const double h = 1.0 / N;
@@ -87,7 +86,7 @@ __global__ void k_tab_near(float4* __restrict__ out, int S, int N) {
     const int ix = i % D, iy = (i / D) % D, iz = i / (D * D);
     double v[4];
     if (ix | iy | iz) {
-      gs1(ix * h, iy * h, iz * h, v);
+      green::eval(gs, ix * h, iy * h, iz * h, v);
     } else {
       v[0] = -cube_mean_inv_r() * (double)N / (4.0 * kPi);
       v[1] = v[2] = v[3] = 0.0;
@@ -99,14 +98,15 @@ __global__ void k_tab_near(float4* __restrict__ out, int S, int N) {
 // The same level table split into BF16 hi + lo per field for the tensor-core
 // M2L: each uint32 holds hi in its low half and lo = bf16(v - hi) in its high
 // half, the four fields in the four words of a uint4.
-__global__ void k_tab_bf16(uint4* __restrict__ out, int p, int level, const float* mlp, int fp32, const float* grid) {
+__global__ void k_tab_bf16(uint4* __restrict__ out, int p, int level, const float* mlp, int fp32, const float* grid,
+                           green::Spec gs) {
   const int hw = 4 * p - 1, E = 8 * p - 1;
   const long total = (long)E * E * E;
   const double dx = 1.0 / ((double)(1 << level) * p);
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     const int ix = (int)(i % E) - hw, iy = (int)((i / E) % E) - hw, iz = (int)(i / ((long)E * E)) - hw;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-    if (ix | iy | iz) gs1(ix * dx, iy * dx, iz * dx, v);
+    if (ix | iy | iz) green::eval(gs, ix * dx, iy * dx, iz * dx, v);
     add_correction(v, ix, iy, iz, level, p, mlp, fp32);
     add_grid(v, ix, iy, iz, level, p, grid);
     uint32_t w[4];
@@ -146,8 +146,19 @@ __global__ void k_grid_grad(const float* __restrict__ dT, int p, int level, floa
   }
 }
 
+// The corrections (network, grid) are corrections of G_S1: they apply only
+// when the plan tabulates G_S1 with periodic boundaries.
+bool plain_gs1(const Plan& P) { return P.gspec.kind == 0 && !P.iso; }
 const float* grid_of(const Plan& P, int level) {
-  return P.has_grid ? P.grid + (size_t)(level - 2) * grid_level_size(P.p) : nullptr;
+  return P.has_grid && plain_gs1(P) ? P.grid + (size_t)(level - 2) * grid_level_size(P.p) : nullptr;
+}
+const float* mlp_of(const Plan& P) { return P.has_corr && plain_gs1(P) ? P.corr_w : nullptr; }
+// The function the tables hold: G_0 in the isolated problem.
+green::Spec spec_of(const Plan& P) {
+  if (!P.iso) return P.gspec;
+  green::Spec g;
+  g.kind = 2;
+  return g;
 }
 
 }  // namespace
@@ -162,19 +173,19 @@ cudaError_t launch_grid_grad(Plan& P, float* grad, cudaStream_t s) {
 }
 
 cudaError_t launch_tab_bf16(Plan& P, int level, cudaStream_t s) {
-  k_tab_bf16<<<4 * P.num_sms, 256, 0, s>>>(P.tab_bf[level], P.p, level, P.has_corr ? P.corr_w : nullptr,
-                                           P.corr_fp32, grid_of(P, level));
+  k_tab_bf16<<<4 * P.num_sms, 256, 0, s>>>(P.tab_bf[level], P.p, level, mlp_of(P), P.corr_fp32, grid_of(P, level),
+                                           spec_of(P));
   return cudaGetLastError();
 }
 
 cudaError_t launch_tables(Plan& P, cudaStream_t s) {
   for (int l = 2; l <= P.L; ++l) {
-    k_tab_m2l<<<4 * P.num_sms, 256, 0, s>>>(P.tab[l], P.tab_lo[l], P.p, l, P.has_corr ? P.corr_w : nullptr,
-                                            P.corr_fp32, grid_of(P, l));
+    k_tab_m2l<<<4 * P.num_sms, 256, 0, s>>>(P.tab[l], P.tab_lo[l], P.p, l, mlp_of(P), P.corr_fp32, grid_of(P, l),
+                                            spec_of(P));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  k_tab_near<<<P.num_sms, 256, 0, s>>>(P.near_tab, P.S, P.N);
+  k_tab_near<<<P.num_sms, 256, 0, s>>>(P.near_tab, P.S, P.N, spec_of(P));
   return cudaGetLastError();
 }
 

@@ -206,3 +206,18 @@ def test_planted_sign_mistake_in_m2l_is_caught(monkeypatch):
     phi, g = fmm.solve(rho, 2, 2)
     p_ref, g_ref = pm.direct(pm.masses(rho), green.g_s1, green.grad_g_s1, green.self_term(n))
     assert _rel(g, g_ref) > 1e-3
+
+
+def test_solve_at_cells_matches_full_solve():
+    # the cell-sampled evaluation returns the full solve's values at those cells
+    N, L, p = 16, 2, 3
+    rho = inputs.lognormal(N, sigma=0.5, seed=31)
+    phi, g = fmm.solve(rho, L, p)
+    leaves = np.array([[0, 3, 1], [3, 3, 3]])
+    cells = np.array([1, 9, 40, 63])
+    S = N >> L
+    full = np.concatenate([phi[None], g])
+    want = np.stack([full[:, a * S:(a + 1) * S, b * S:(b + 1) * S, c * S:(c + 1) * S].reshape(4, -1)
+                     for a, b, c in leaves])[:, :, cells]
+    got = fmm.solve_at(rho, L, p, leaves, cells=cells)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())

@@ -165,3 +165,21 @@ def test_gerr_of_g_s1_is_within_the_stated_accuracy_from_six_multipoles():
         assert (lmax < 1e-3) == (t_lmax < 1e-3) and (l2 < 1e-4) == (t_l2 < 1e-4), (p, lmax, l2)
         if p == 6:
             assert npo.me_error(terms[2], terms[3])[0] > lmax
+
+
+def test_sampled_isolated_solve_equals_the_full_one():
+    # solve_isolated_at (leaves, and cells within them) must return exactly
+    # what solve_isolated computes there
+    N, L, p = 16, 2, 3
+    rho = inputs.plummer(N, n_clumps=3, seed=12, a_min=0.5, a_max=2.0)
+    phi, g = npo.solve_isolated(rho, L, p)
+    leaves = np.array([[0, 0, 0], [3, 1, 2], [2, 3, 3]])
+    cells = np.array([0, 5, 17, 63])
+    S = N >> L
+    full = np.concatenate([phi[None], g])
+    want = np.stack([full[:, a * S:(a + 1) * S, b * S:(b + 1) * S, c * S:(c + 1) * S].reshape(4, -1)
+                     for a, b, c in leaves])
+    got = npo.solve_isolated_at(rho, L, p, leaves)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+    got_c = npo.solve_isolated_at(rho, L, p, leaves, cells)
+    np.testing.assert_allclose(got_c, want[:, :, cells], rtol=1e-12, atol=1e-12 * np.abs(want).max())
