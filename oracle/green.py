@@ -46,6 +46,54 @@ def dxi_s1(t):
     return (1.0 - a1) * np.cos(np.pi * t) + a1 * np.cos(3.0 * np.pi * t)
 
 
+def xi_ansatz(t, a):
+    """xi_n(t) of the Sec. 3 ansatz with coefficients a = (a_1, ..., a_n):
+    sin(pi t)/pi + sum_k a_k (sin((2k+1) pi t)/((2k+1) pi) - sin(pi t)/pi)."""
+    t = np.asarray(t, dtype=np.float64)
+    s1 = np.sin(np.pi * t) / np.pi
+    out = s1.copy()
+    for k, ak in enumerate(a, start=1):
+        m = 2 * k + 1
+        out += ak * (np.sin(m * np.pi * t) / (m * np.pi) - s1)
+    return out
+
+
+def dxi_ansatz(t, a):
+    """d xi_n / dt = cos(pi t) + sum_k a_k (cos((2k+1) pi t) - cos(pi t))."""
+    t = np.asarray(t, dtype=np.float64)
+    c1 = np.cos(np.pi * t)
+    out = c1.copy()
+    for k, ak in enumerate(a, start=1):
+        out += ak * (np.cos((2 * k + 1) * np.pi * t) - c1)
+    return out
+
+
+def g_s(x, a, self_value=None):
+    """G_S(x) = -1/(4 pi |xhat|), xhat_i = xi_n(x_i) with coefficients a
+    (Sec. 3 ansatz); ``self_value`` at x = 0 as in g_s1."""
+    xh = xi_ansatz(np.asarray(x, dtype=np.float64), a)
+    r = np.sqrt(np.sum(xh * xh, axis=-1))
+    zero = r == 0.0
+    if np.any(zero) and self_value is None:
+        raise ValueError("G_S evaluated at 0 without a self-term value")
+    out = np.empty_like(r)
+    out[~zero] = -1.0 / (FOUR_PI * r[~zero])
+    out[zero] = self_value if self_value is not None else 0.0
+    return out
+
+
+def grad_g_s(x, a):
+    """grad G_S by the chain rule; 0 at x = 0."""
+    x = np.asarray(x, dtype=np.float64)
+    xh = xi_ansatz(x, a)
+    r2 = np.sum(xh * xh, axis=-1)
+    zero = r2 == 0.0
+    r3 = np.where(zero, 1.0, r2 * np.sqrt(r2))
+    out = xh * dxi_ansatz(x, a) / (FOUR_PI * r3[..., None])
+    out[zero] = 0.0
+    return out
+
+
 def g_s1(x, self_value=None):
     """G_S1(x) = -1/(4 pi |xhat <> L|), xhat_i = L xi_s1(x_i/L)  (eq. gfs1, Sec. 4).
 

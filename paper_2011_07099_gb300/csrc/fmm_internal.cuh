@@ -98,7 +98,7 @@ struct Plan {
   void* Mbf_hi[kMaxLevel + 1] = {};        // gridlet masses split into bf16 hi / lo (interleaved per 8), rows padded
   void* Mbf_lo[kMaxLevel + 1] = {};        // unused (kept null)
   void* Apre[kMaxLevel + 1] = {};          // precomputed split translation tiles per offset slot
-  int tc_group = 2;                        // offsets accumulated per TMEM partial before promotion
+  int tc_group = 4;                        // offsets accumulated per TMEM partial before promotion
   int tc_min_level = kTcMinLevel;          // first level on the tensor cores in the mixed forms
   // learned table correction (MLP weights) and its training buffers
   float* corr_w = nullptr;                 // mlp::kParams weights (device) or unset

@@ -14,22 +14,26 @@
 // memory tile layout (`k_build_a`), and each pipeline stage streams its two
 // 8 KB tiles with one bulk asynchronous copy.
 //
-// CTA tile: 128 rows of (f, r) x 128 targets.  Warp roles:
+// CTA tile: 128 rows of (f, r) x 256 targets (one M = 128, N = 256 MMA per
+// 16-deep k step, so every A byte staged feeds 256 targets).  Warp roles:
 //   warp 0      issues the MMAs (one thread);
 //   warps 1..4  per stage (32 reduction indices of one offset): one thread
-//               arms the stage barrier with the A bytes and issues the bulk
-//               copies; all gather B, the source nodes' split BF16 masses,
-//               with 16-byte cp.async whose completion arrives on the stage
-//               barrier (hi and lo are interleaved every 8 values, so a
+//               arms the stage's A barrier with the A bytes and issues the
+//               bulk copies; all gather B, the source nodes' split BF16
+//               masses, with 16-byte cp.async whose completion arrives on the
+//               stage barrier (hi and lo are interleaved every 8 values, so a
 //               target's stage slice is one 128-byte line);
 //   warps 5..8  drain TMEM: every G offsets accumulate into a fresh TMEM
-//               partial (two buffers, ping-pong), and the drain warps add the
-//               finished partial into a Kahan-compensated FP32 total kept in
-//               TMEM.  A single TMEM accumulator over all 189 p^3 terms
-//               drifts by ~1e-4 on the coherent, cancelling far-field sums.
+//               partial, which the drain warps add into an FP32 total kept in
+//               TMEM while the issuer waits.  A single TMEM accumulator over
+//               all 189 p^3 terms drifts by ~1e-4 on the coherent, cancelling
+//               far-field sums (the accumulation inside the MMA truncates);
+//               per-group partials summed in FP32 with rounding to nearest
+//               cost ~1e-7 (CPU emulation of the level's sums), far below the
+//               bf16x3 operand error.
 // Layout: canonical no-swizzle K-major core matrices (8 rows x 16 B).
 // bf16x3 mode accumulates A_hi B_hi + A_hi B_lo + A_lo B_hi; bf16 mode A_hi B_hi.
-// TMEM: 512 columns = partial[0] | partial[1] | total | compensation.
+// TMEM: 512 columns = partial (256) | total (256).
 // Every wait is bounded; a timeout sets the plan's error word and later work
 // is skipped without leaving any barrier sequence.  Before the CTA exits the
 // issuer waits (bounded) for the completion of every MMA it issued and the
@@ -44,12 +48,13 @@ namespace fmm {
 namespace {
 
 constexpr int kKC = 32;          // reduction indices per pipeline stage
-constexpr int kNT = 128;         // targets per CTA
+constexpr int kNT = 256;         // targets per CTA (MMA N)
 constexpr int kProd = 128;       // producer threads (warps 1..4)
 constexpr int kDrain = 128;      // drain threads (warps 5..8)
 constexpr int kThreads = 32 + kProd + kDrain;
 constexpr uint32_t kTmemCols = 512;
-constexpr int kTileBytes = 128 * kKC * 2;     // one 128 x 32 BF16 operand tile
+constexpr int kTileBytes = 128 * kKC * 2;     // one 128 x 32 BF16 tile of A
+constexpr int kTileB = kNT * kKC * 2;         // one 256 x 32 BF16 tile of B
 
 template <int P, int MODE>
 struct TcShape {
@@ -58,7 +63,7 @@ struct TcShape {
   static constexpr int NCH = KP / kKC;                       // stages per offset
   static constexpr int MT = (4 * P3 + 127) / 128;            // row tiles
   static constexpr int NSPLIT = MODE == 3 ? 2 : 1;
-  static constexpr int STAGE_BYTES = NSPLIT * 2 * kTileBytes;
+  static constexpr int STAGE_BYTES = NSPLIT * (kTileBytes + kTileB);
   static constexpr int EXTRA = 2 * kNT * 4 + 64;
   static constexpr int LIMIT = 225 * 1024;                  // dynamic shared memory budget
   static constexpr int FIT = (LIMIT - EXTRA) / STAGE_BYTES;
@@ -83,21 +88,23 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
   constexpr int STAGE_BYTES = Sh::STAGE_BYTES;
   static_assert(Sh::SMEM <= Sh::LIMIT, "shared-memory budget");
   constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, kNT);
-  constexpr uint32_t LBO = (128 / 8) * 128;        // next core matrix along K (A and B tiles alike)
+  constexpr uint32_t LBO_A = (128 / 8) * 128;      // next core matrix along K in an A tile
+  constexpr uint32_t LBO_B = (kNT / 8) * 128;      // next core matrix along K in a B tile
   constexpr uint32_t A_TX = NSPLIT * kTileBytes;
 
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* stages = smem;                                                // ST * STAGE_BYTES: A tiles | B tiles
+  uint8_t* stages = smem;                                                // ST x [A tiles | B tiles]
   int* srckey = reinterpret_cast<int*>(smem + ST * STAGE_BYTES);         // 2 x kNT
   // full: the producers' cp.async gathers of B landed; afull: the bulk copy of
   // A landed (its own barrier, so that a CTA that gives up can still wait for
-  // exactly the copies it issued); empty: the MMAs reading the stage are done.
-  __shared__ uint64_t full[ST], afull[ST], empty[ST], pfull[2], pfree[2], mdone;
+  // exactly the copies it issued); empty: the MMAs reading the stage are done;
+  // pfull / pfree: a group's partial is complete / has been added to the total.
+  __shared__ uint64_t full[ST], afull[ST], empty[ST], pfull, pfree, mdone;
   __shared__ uint32_t tmem_holder;
   __shared__ int s_err;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int mt = blockIdx.x, nt = blockIdx.y, ctype = blockIdx.z;
+  const int nt = blockIdx.x, mt = blockIdx.y, ctype = blockIdx.z;
   const int n = 1 << level;
   const uint32_t n_par = 1u << (3 * (level - 1));
   const uint32_t par0 = (uint32_t)nt * kNT;
@@ -111,10 +118,8 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
       tc::mbar_init(&afull[i], 1);             // the A expect_tx arrival (+ its bytes)
       tc::mbar_init(&empty[i], 1);             // one MMA completion
     }
-    for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(&pfull[b], 1);
-      tc::mbar_init(&pfree[b], kDrain);
-    }
+    tc::mbar_init(&pfull, 1);
+    tc::mbar_init(&pfree, kDrain);
     tc::mbar_init(&mdone, 1);
     tc::mbar_fence_init();
   }
@@ -123,7 +128,7 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_holder;
-  const uint32_t t_tot = tmem + 256, t_cmp = tmem + 384;
+  const uint32_t t_tot = tmem + kNT;
   const uint32_t smem_base = tc::smem_u32(stages);
 
   if (warp == 0) {
@@ -133,14 +138,14 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
     if (lane == 0) {
       bool ok = true;
       for (int io = 0; io < n_off && ok && !stall; ++io) {
-        const int g = io / group, b = g & 1;
+        const int g = io / group;
         const bool first = (io % group) == 0;
-        if (first && g >= 2 && !tc::mbar_wait_bounded(&pfree[b], (uint32_t)((g - 2) >> 1) & 1u, kWaitNs)) {
+        // the partial is reused: the drain must have added group g - 1
+        if (first && g >= 1 && !tc::mbar_wait_bounded(&pfree, (uint32_t)(g - 1) & 1u, kWaitNs)) {
           ok = false;
           break;
         }
         tc::fence_after_sync();
-        const uint32_t dst = tmem + (uint32_t)(b * kNT);
         for (int ch = 0; ch < NCH; ++ch) {
           const int it = io * NCH + ch, st = it % ST;
           const uint32_t ph = (uint32_t)(it / ST) & 1u;
@@ -154,19 +159,19 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
           const uint32_t sB = sA + NSPLIT * kTileBytes;
 #pragma unroll
           for (int j = 0; j < kKC / 16; ++j) {
-            const uint64_t ah = tc::smem_desc(sA + j * 2 * LBO, LBO, 128);
-            const uint64_t bh = tc::smem_desc(sB + j * 2 * LBO, LBO, 128);
-            tc::mma_bf16(dst, ah, bh, IDESC, (!first || ch > 0 || j > 0) ? 1u : 0u);
+            const uint64_t ah = tc::smem_desc(sA + j * 2 * LBO_A, LBO_A, 128);
+            const uint64_t bh = tc::smem_desc(sB + j * 2 * LBO_B, LBO_B, 128);
+            tc::mma_bf16(tmem, ah, bh, IDESC, (!first || ch > 0 || j > 0) ? 1u : 0u);
             if (MODE == 3) {
-              const uint64_t al = tc::smem_desc(sA + kTileBytes + j * 2 * LBO, LBO, 128);
-              const uint64_t bl = tc::smem_desc(sB + kTileBytes + j * 2 * LBO, LBO, 128);
-              tc::mma_bf16(dst, ah, bl, IDESC, 1u);
-              tc::mma_bf16(dst, al, bh, IDESC, 1u);
+              const uint64_t al = tc::smem_desc(sA + kTileBytes + j * 2 * LBO_A, LBO_A, 128);
+              const uint64_t bl = tc::smem_desc(sB + kTileB + j * 2 * LBO_B, LBO_B, 128);
+              tc::mma_bf16(tmem, ah, bl, IDESC, 1u);
+              tc::mma_bf16(tmem, al, bh, IDESC, 1u);
             }
           }
           tc::mma_commit(&empty[st]);
         }
-        if (ok && ((io % group) == group - 1 || io == n_off - 1)) tc::mma_commit(&pfull[b]);
+        if (ok && ((io % group) == group - 1 || io == n_off - 1)) tc::mma_commit(&pfull);
       }
       // every MMA this thread issued has finished before TMEM is released,
       // also when a wait gave up part-way
@@ -186,18 +191,20 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
       const int ox = my_offs[3 * io + 0], oy = my_offs[3 * io + 1], oz = my_offs[3 * io + 2];
       // source keys of this offset (buffer b was last read two offsets ago)
       producer_bar();
-      {
+#pragma unroll
+      for (int h = 0; h < kNT / kProd; ++h) {
+        const int t = pt + h * kProd;
         int key = -1;
-        if (par0 + pt < n_par) {
+        if (par0 + t < n_par) {
           uint32_t x, y, z;
-          unmorton(8u * (par0 + pt) + ctype, x, y, z);
+          unmorton(8u * (par0 + t) + ctype, x, y, z);
           // the source node, wrapped; in the isolated problem a source
           // outside the box contributes nothing (zero-filled like padding)
           const int ux = (int)x - ox, uy = (int)y - oy, uz = (int)z - oz;
           const bool inbox = (unsigned)ux < (unsigned)n && (unsigned)uy < (unsigned)n && (unsigned)uz < (unsigned)n;
           if (inbox || !iso) key = (int)morton((uint32_t)ux & (n - 1), (uint32_t)uy & (n - 1), (uint32_t)uz & (n - 1));
         }
-        srckey[b * kNT + pt] = key;
+        srckey[b * kNT + t] = key;
       }
       producer_bar();
       const int* sk = srckey + b * kNT;
@@ -216,12 +223,12 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
           armed = it + 1;
         }
 #pragma unroll
-        for (int pass = 0; pass < 8; ++pass) {
+        for (int pass = 0; pass < kNT / 16; ++pass) {
           const int t = (pt >> 3) + 16 * pass;
           if (MODE == 3 || split == 0) {
             const int key = sk[t];
             const size_t e0 = ((size_t)(key < 0 ? 0 : key) * (KP / 8) + ch * (kKC / 8) + c8) * 16 + split * 8;
-            const uint32_t d = sB + split * kTileBytes + (uint32_t)((c8 * (kNT / 8) + t / 8) * 128 + (t % 8) * 16);
+            const uint32_t d = sB + split * kTileB + (uint32_t)((c8 * (kNT / 8) + t / 8) * 128 + (t % 8) * 16);
             tc::cp_async16(d, Msp + e0, key < 0 ? 0u : 16u);
           }
         }
@@ -244,56 +251,37 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
     const uint32_t lanebase = (uint32_t)(q * 32) << 16;
     bool ok = true;
     for (int g = 0; g < n_grp; ++g) {
-      const int b = g & 1;
-      const bool got = ok && tc::mbar_wait_bounded(&pfull[b], (uint32_t)(g >> 1) & 1u, kWaitNs);
+      const bool got = ok && tc::mbar_wait_bounded(&pfull, (uint32_t)g & 1u, kWaitNs);
       ok = __all_sync(0xffffffffu, got);
       if (!ok) break;
       tc::fence_after_sync();
-      const uint32_t tp = tmem + lanebase + (uint32_t)(b * kNT);
       for (int c0 = 0; c0 < kNT; c0 += 32) {
-        uint32_t rp[32], rt[32], rc[32];
-        tc::tmem_ld32_nowait(tp + c0, rp);
-        if (g > 0) {
-          tc::tmem_ld32_nowait(t_tot + lanebase + c0, rt);
-          tc::tmem_ld32_nowait(t_cmp + lanebase + c0, rc);
-        }
+        uint32_t rp[32], rt[32];
+        tc::tmem_ld32_nowait(tmem + lanebase + c0, rp);
+        if (g > 0) tc::tmem_ld32_nowait(t_tot + lanebase + c0, rt);
         tc::tmem_wait_ld();
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const float x = __uint_as_float(rp[k]);
-          if (g == 0) {
-            rt[k] = rp[k];
-            rc[k] = 0u;
-          } else {
-            const float tot = __uint_as_float(rt[k]), c = __uint_as_float(rc[k]);
-            const float y = x - c;
-            const float t = tot + y;
-            rc[k] = __float_as_uint((t - tot) - y);
-            rt[k] = __float_as_uint(t);
-          }
-        }
+        for (int k = 0; k < 32; ++k)
+          rt[k] = g == 0 ? rp[k] : __float_as_uint(__uint_as_float(rt[k]) + __uint_as_float(rp[k]));
         tc::tmem_st32(t_tot + lanebase + c0, rt);
-        tc::tmem_st32(t_cmp + lanebase + c0, rc);
       }
       tc::tmem_wait_st();
       tc::fence_before_sync();
-      tc::mbar_arrive(&pfree[b]);
+      tc::mbar_arrive(&pfree);
     }
-    // final: F = total - compensation
+    // final: F = total
     if (ok && n_off > 0 && __all_sync(0xffffffffu, atomicAdd(&s_err, 0) == 0)) {
       const int m = q * 32 + lane;
       const int gm = mt * 128 + m;
       for (int c0 = 0; c0 < kNT; c0 += 32) {
-        uint32_t rt[32], rc[32];
+        uint32_t rt[32];
         tc::tmem_ld32_nowait(t_tot + lanebase + c0, rt);
-        tc::tmem_ld32_nowait(t_cmp + lanebase + c0, rc);
         tc::tmem_wait_ld();
         if (gm < 4 * P3) {
 #pragma unroll
           for (int k = 0; k < 32; ++k) {
             const uint32_t t = par0 + c0 + k;
-            if (t < n_par)
-              F[(size_t)(8u * t + ctype) * 4 * P3 + gm] = __uint_as_float(rt[k]) - __uint_as_float(rc[k]);
+            if (t < n_par) F[(size_t)(8u * t + ctype) * 4 * P3 + gm] = __uint_as_float(rt[k]);
           }
         }
       }
@@ -368,7 +356,9 @@ cudaError_t setup_one() {
 template <int P, int MODE>
 cudaError_t launch_one(Plan& Pl, int level, cudaStream_t s) {
   const uint32_t n_par = 1u << (3 * (level - 1));
-  dim3 grid(TcShape<P, MODE>::MT, (n_par + kNT - 1) / kNT, 8);
+  // target tiles fastest: the CTAs in flight share row tile and child type,
+  // hence their A tiles, which L2 then serves to all of them
+  dim3 grid((n_par + kNT - 1) / kNT, TcShape<P, MODE>::MT, 8);
   const __nv_bfloat16* Msp = static_cast<const __nv_bfloat16*>(Pl.Mbf_hi[level]);
   const uint8_t* Apre = static_cast<const uint8_t*>(Pl.Apre[level]);
   k_m2l_tc<P, MODE><<<grid, kThreads, smem_bytes<P, MODE>(), s>>>(

@@ -245,17 +245,22 @@ k_p2p(const float* __restrict__ rho, const double* __restrict__ mean, int N, int
 // chunk; the sign of dx is the same for the whole chunk except in the
 // target's own chunk (base 0), where it is resolved at compile time.  The
 // summation keeps the row -> plane -> total partial sums of the kernel above.
+// L2P runs in double-float here: the cells at the edges of a 16-cell leaf lie
+// well outside the order-p gridlet's hull (absolute weight sums up to 835 at
+// p = 6 against 46 for 8-cell leaves), which amplifies the rounding of FP32
+// partial sums to ~1e-5 of the potential at the leaf corners.
 constexpr int kS16 = 16, kW16 = 48, kT16 = 256;
 
 struct P2P16Smem {
-  int far, w8, t1, t2, in, pl0, pl1, total;   // offsets in floats
+  int far, w8, t1, t2, o2, in2, pl0, pl1, total;   // offsets in floats
   __host__ __device__ P2P16Smem(int p) {
-    far = 0;
-    w8 = 4 * kS16 * kS16 * kS16;
-    t1 = w8 + 2 * p * kS16;
-    t2 = t1 + 4 * p * p * kS16;
-    in = (t2 + 4 * p * kS16 * kS16 + 3) / 4 * 4;
-    pl0 = in + 4 * p * p * p;
+    far = 0;                                      // 4 S^3 floats
+    w8 = 4 * kS16 * kS16 * kS16;                  // p S float2
+    t1 = w8 + 2 * p * kS16;                       // p p S float2
+    t2 = t1 + 2 * p * p * kS16;                   // p S S float2
+    o2 = t2 + 2 * p * kS16 * kS16;                // S^3 float2
+    in2 = o2 + 2 * kS16 * kS16 * kS16;            // p^3 float2
+    pl0 = (in2 + 2 * p * p * p + 3) / 4 * 4;
     pl1 = pl0 + kW16 * kW16;
     total = pl1 + kW16 * kW16;
   }
@@ -326,10 +331,20 @@ k_p2p16(const float* __restrict__ rho, const double* __restrict__ mean, int N, i
 
   fetch(0, 0);
   for (int i = tid; i < p * kS16; i += nthr) W8[i] = wp2m[i];
-  for (int i = tid; i < 4 * p3; i += nthr) base[lay.in + i] = Fleaf[(size_t)leaf * 4 * p3 + i];
-  __syncthreads();
-  // L2P of the whole leaf (ends with a barrier)
-  contract3(base + lay.in, base + lay.t1, base + lay.t2, far, 4, p, kS16, W8, kS16, true, tid, nthr);
+  // L2P of the whole leaf, one field at a time, in double-float
+  {
+    float2* in2 = reinterpret_cast<float2*>(base + lay.in2);
+    float2* o2 = reinterpret_cast<float2*>(base + lay.o2);
+    constexpr int S3 = kS16 * kS16 * kS16;
+    for (int f = 0; f < 4; ++f) {
+      for (int i = tid; i < p3; i += nthr) in2[i] = make_float2(Fleaf[((size_t)leaf * 4 + f) * p3 + i], 0.f);
+      __syncthreads();
+      contract3_df(in2, reinterpret_cast<float2*>(base + lay.t1), reinterpret_cast<float2*>(base + lay.t2), o2, p,
+                   kS16, W8, kS16, true, tid, nthr);      // ends with a barrier
+      for (int i = tid; i < S3; i += nthr) far[f * S3 + i] = o2[i].x + o2[i].y;
+    }
+    __syncthreads();
+  }
 
   const int row = tid & 127, h = tid >> 7;
   const int cz = zh * 8 + (row >> 4), cy = row & 15;

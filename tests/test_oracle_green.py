@@ -119,3 +119,29 @@ def test_g_k_single_mode_closed_form():
     np.testing.assert_allclose(g[0], gx_exact, atol=1e-14)
     np.testing.assert_allclose(g[2], -3 * gx_exact, atol=1e-14)
     assert abs(phi.mean()) < 1e-16
+
+
+def test_ansatz_is_newtonian_at_small_scales_and_smooth_at_half_the_box():
+    # Sec. 3: for any a_k, xhat -> x at small scales and xi_n is differentiable
+    # (zero slope) at half the box; a_1 = -1/8 is G_S1
+    rng = np.random.default_rng(3)
+    t = np.array([1e-5, -2e-5])
+    for a in ([-0.125], [-0.12], [0.05, -0.02], list(rng.normal(0, 0.1, 4))):
+        np.testing.assert_allclose(green.xi_ansatz(t, a), t, rtol=1e-8)
+        np.testing.assert_allclose(green.dxi_ansatz(np.array([0.5, -0.5]), a), 0.0, atol=1e-15)
+        np.testing.assert_allclose(green.xi_ansatz(t + 1.0, a), -green.xi_ansatz(t, a), rtol=1e-6, atol=1e-15)
+    x = rng.uniform(-0.5, 0.5, (50, 3))
+    np.testing.assert_allclose(green.g_s(x, [-0.125]), green.g_s1(x), rtol=1e-14)
+    np.testing.assert_allclose(green.grad_g_s(x, [-0.125]), green.grad_g_s1(x), rtol=1e-12, atol=1e-14)
+
+
+def test_ansatz_gradient_is_the_derivative_of_the_ansatz():
+    rng = np.random.default_rng(4)
+    a = [-0.12, 0.03]
+    x = rng.uniform(-0.45, 0.45, (20, 3))
+    h = 1e-6
+    for i in range(3):
+        e = np.zeros(3)
+        e[i] = h
+        fd = (green.g_s(x + e, a) - green.g_s(x - e, a)) / (2 * h)
+        np.testing.assert_allclose(green.grad_g_s(x, a)[:, i], fd, rtol=1e-6, atol=1e-9)
