@@ -132,11 +132,24 @@ int fmm_plan_set_boundary(fmm_plan* plan, int boundary);
  * FMM_GREEN_S1 (default): G_S1 of eq. gfs1.  FMM_GREEN_S: the ansatz G_S of
  * Sec. 3, xi_n(t) = sin(pi t)/pi + sum_k a_k (sin((2k+1) pi t)/((2k+1) pi)
  * - sin(pi t)/pi) with a[0..na-1] = a_1..a_na, 1 <= na <= 4 (G_S1 is na = 1,
- * a_1 = -1/8); used to fit a_k (Table 1).  Corrections (network, grid) apply
+ * a_1 = -1/8); used to fit a_k (Table 1).  FMM_GREEN_X: the exact-in-real-
+ * space G_X = -1/(4 pi |x <> L|) of eq. gfx (a and na ignored), whose kink
+ * at half the box aliases (Fig. errex).  Corrections (network, grid) apply
  * to G_S1 only.  Re-tabulates (synchronous).  FMM_ERR_ARG otherwise. */
 #define FMM_GREEN_S1 0
 #define FMM_GREEN_S  1
+#define FMM_GREEN_X  2
 int fmm_plan_set_green(fmm_plan* plan, int kind, const double* a, int na);
+
+/* Any periodic Green's function given on the N^3 mesh, e.g. the exact-in-
+ * Fourier-space G_K of eq. gfk (whose real-space values have no closed form):
+ * mesh (device or host, 4 N^3 doubles, copied) holds G, -dG/dx, -dG/dy,
+ * -dG/dz at the offsets d/N, d in [0, N)^3, x fastest, d = 0 holding the cell
+ * self term (the layout fmm_plan_mesh_green writes).  Every table entry is
+ * then a mesh value, which needs every gridlet point on a cell centre: the
+ * leaf size S must be a multiple of the order (FMM_ERR_ARG otherwise, and
+ * for n != 4 N^3).  Re-tabulates (synchronous). */
+int fmm_plan_set_green_mesh(fmm_plan* plan, const double* mesh, size_t n);
 
 /* The plan's Green's function sampled on a mesh, for PM references (Sec. 3:
  * PM and FMM with the same G).  Periodic plans: M = N, entries at offsets

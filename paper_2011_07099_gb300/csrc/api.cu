@@ -131,6 +131,7 @@ void free_plan(Plan* P) {
   cudaFree(P->dT_all);
   cudaFree(P->grad_partials);
   cudaFree(P->grid);
+  cudaFree(P->gmesh);
   for (int l = 0; l <= fmm::kMaxLevel; ++l) cudaFree(P->lam[l]);
   for (int l = 0; l <= fmm::kMaxLevel; ++l) {
     cudaFree(P->tab_bf[l]);
@@ -420,13 +421,27 @@ int fmm_plan_set_boundary(fmm_plan* plan, int boundary) {
 }
 
 int fmm_plan_set_green(fmm_plan* plan, int kind, const double* a, int na) {
-  if (!plan || (kind != FMM_GREEN_S1 && kind != FMM_GREEN_S)) return set_err(FMM_ERR_ARG);
+  if (!plan || (kind != FMM_GREEN_S1 && kind != FMM_GREEN_S && kind != FMM_GREEN_X)) return set_err(FMM_ERR_ARG);
   if (kind == FMM_GREEN_S && (na < 1 || na > fmm::green::kMaxAnsatz || !a)) return set_err(FMM_ERR_ARG);
   Plan& P = *reinterpret_cast<Plan*>(plan);
   fmm::green::Spec g;
-  g.kind = kind == FMM_GREEN_S ? 1 : 0;
+  g.kind = kind == FMM_GREEN_S ? 1 : (kind == FMM_GREEN_X ? 3 : 0);
   g.na = kind == FMM_GREEN_S ? na : 0;
   for (int k = 0; k < g.na; ++k) g.a[k] = a[k];
+  P.gspec = g;
+  return set_err(retabulate(P));
+}
+
+int fmm_plan_set_green_mesh(fmm_plan* plan, const double* mesh, size_t n) {
+  if (!plan || !mesh) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  const size_t n3 = (size_t)P.N * P.N * P.N;
+  // every gridlet point of every level must sit on a mesh cell centre
+  if (n != 4 * n3 || P.S % P.p != 0) return set_err(FMM_ERR_ARG);
+  if (!P.gmesh && !dev_alloc(&P.gmesh, 4 * n3)) return set_err(FMM_ERR_ALLOC);
+  FMM_CUDA_TRY(cudaMemcpy(P.gmesh, mesh, sizeof(double) * 4 * n3, cudaMemcpyDefault));
+  fmm::green::Spec g;
+  g.kind = 4;
   P.gspec = g;
   return set_err(retabulate(P));
 }

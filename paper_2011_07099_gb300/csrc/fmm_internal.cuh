@@ -68,6 +68,7 @@ struct Plan {
   // interaction and near zones keep only in-box nodes
   green::Spec gspec;
   int iso = 0;
+  double* gmesh = nullptr;          // kind 4: (G, -dG/dx, -dG/dy, -dG/dz) at the mesh offsets, 4 N^3
   int device = 0;
   int num_sms = 0;
   int solved = 0;

@@ -14,6 +14,11 @@
 //
 // G_0 = -1/(4 pi r), the Newtonian Green's function of the isolated
 // (non-periodic) problem of Sec. 3's accuracy experiment (eq. gerr).
+//
+// G_X = -1/(4 pi |x <> L|), the "exact-in-real-space" periodic function of
+// Sec. 1 (eq. gfx): the displacement wrapped to its nearest image.  It has a
+// kink where a wrapped component is +-L/2 (the aliasing of Fig. errex); there
+// the gradient component is taken as the mean of the two one-sided values, 0.
 #pragma once
 
 namespace fmm {
@@ -25,7 +30,7 @@ constexpr int kMaxAnsatz = 4;     // coefficients a_1..a_4 of the G_S ansatz
 // Which function a plan tabulates (FMM_GREEN_* of fmm.h), with the ansatz
 // coefficients of G_S.
 struct Spec {
-  int kind = 0;                   // 0 G_S1, 1 G_S(a), 2 G_0
+  int kind = 0;                   // 0 G_S1, 1 G_S(a), 2 G_0, 3 G_X, 4 sampled on the mesh
   int na = 0;
   double a[kMaxAnsatz] = {0.0, 0.0, 0.0, 0.0};
 };
@@ -90,12 +95,26 @@ __device__ inline void g0(double x, double y, double z, double out[4]) {
   out[3] = c * z;
 }
 
-// Dispatch on the plan's function; x != 0.
+// The same four values for G_X.
+__device__ inline void gx(double x, double y, double z, double out[4]) {
+  const double w[3] = {x - rint(x), y - rint(y), z - rint(z)};
+  const double r2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  const double r = sqrt(r2);
+  const double inv4pi = 1.0 / (4.0 * kPi);
+  out[0] = -inv4pi / r;
+  const double c = -inv4pi / (r2 * r);
+  for (int i = 0; i < 3; ++i) out[1 + i] = fabs(w[i]) == 0.5 ? 0.0 : c * w[i];
+}
+
+// Dispatch on the plan's analytic function; x != 0.  (A function sampled on
+// the mesh, kind 4, is looked up by the table kernels instead.)
 __device__ inline void eval(const Spec& g, double x, double y, double z, double out[4]) {
   if (g.kind == 1)
     gs_ansatz(x, y, z, g, out);
   else if (g.kind == 2)
     g0(x, y, z, out);
+  else if (g.kind == 3)
+    gx(x, y, z, out);
   else
     gs1(x, y, z, out);
 }

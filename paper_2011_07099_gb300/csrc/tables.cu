@@ -55,15 +55,35 @@ __device__ inline void add_grid(double v[4], int ix, int iy, int iz, int level, 
 // (Sec. 3: gridlet spacing of a level-l node; the (4 N_g)^D samples of Sec. 4
 // folded over the sign of each component).  Entry n = 0 is never used by M2L
 // (the interaction zone excludes near nodes) and is stored as 0.
+// A function given on the mesh (kind 4): the value at the cell offset
+// (cx, cy, cz), taken modulo N (periodic).
+__device__ inline void mesh_value(const double* mesh, int N, long cx, long cy, long cz, double v[4]) {
+  const long x = ((cx % N) + N) % N, y = ((cy % N) + N) % N, z = ((cz % N) + N) % N;
+  const size_t n3 = (size_t)N * N * N, e = ((size_t)z * N + y) * N + x;
+  for (int f = 0; f < 4; ++f) v[f] = mesh[f * n3 + e];
+}
+
+// (G, -grad G) of table entry n at level l: analytic at n dx_l, or from the
+// mesh, where gridlet spacing dx_l is cpg = N / (2^l p) whole cells.
+__device__ inline void table_value(const green::Spec& gs, const double* mesh, int N, int level, int p, int ix, int iy,
+                                   int iz, double v[4]) {
+  if (gs.kind == 4) {
+    const long cpg = (long)N / ((long)(1 << level) * p);
+    mesh_value(mesh, N, ix * cpg, iy * cpg, iz * cpg, v);
+  } else {
+    const double dx = 1.0 / ((double)(1 << level) * p);
+    green::eval(gs, ix * dx, iy * dx, iz * dx, v);
+  }
+}
+
 __global__ void k_tab_m2l(float4* __restrict__ out, float4* __restrict__ lo, int p, int level, const float* mlp,
-                          int fp32, const float* grid, green::Spec gs) {
+                          int fp32, const float* grid, green::Spec gs, const double* mesh, int N) {
   const int hw = 4 * p - 1, E = 8 * p - 1;
   const long total = (long)E * E * E;
-  const double dx = 1.0 / ((double)(1 << level) * p);
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     const int ix = (int)(i % E) - hw, iy = (int)((i / E) % E) - hw, iz = (int)(i / ((long)E * E)) - hw;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-    if (ix | iy | iz) green::eval(gs, ix * dx, iy * dx, iz * dx, v);
+    if (ix | iy | iz) table_value(gs, mesh, N, level, p, ix, iy, iz, v);
     add_correction(v, ix, iy, iz, level, p, mlp, fp32);
     add_grid(v, ix, iy, iz, level, p, grid);
     out[i] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
@@ -78,14 +98,16 @@ __global__ void k_tab_m2l(float4* __restrict__ out, float4* __restrict__ lo, int
 // folded: G is even in every component, -dG/dx_i is odd in x_i and even in the
 // others, so entries hold the values at (|dx|, |dy|, |dz|) and the kernel
 // restores the signs.  d = 0 holds the self term -(1/4 pi) <1/r>_cell / h.
-__global__ void k_tab_near(float4* __restrict__ out, int S, int N, green::Spec gs) {
+__global__ void k_tab_near(float4* __restrict__ out, int S, int N, green::Spec gs, const double* mesh) {
   const int D = 2 * S;
   const int total = D * D * D;
   const double h = 1.0 / N;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const int ix = i % D, iy = (i / D) % D, iz = i / (D * D);
     double v[4];
-    if (ix | iy | iz) {
+    if (gs.kind == 4) {
+      mesh_value(mesh, N, ix, iy, iz, v);      // the mesh carries its own self term
+    } else if (ix | iy | iz) {
       green::eval(gs, ix * h, iy * h, iz * h, v);
     } else {
       v[0] = -cube_mean_inv_r() * (double)N / (4.0 * kPi);
@@ -99,14 +121,13 @@ __global__ void k_tab_near(float4* __restrict__ out, int S, int N, green::Spec g
 // M2L: each uint32 holds hi in its low half and lo = bf16(v - hi) in its high
 // half, the four fields in the four words of a uint4.
 __global__ void k_tab_bf16(uint4* __restrict__ out, int p, int level, const float* mlp, int fp32, const float* grid,
-                           green::Spec gs) {
+                           green::Spec gs, const double* mesh, int N) {
   const int hw = 4 * p - 1, E = 8 * p - 1;
   const long total = (long)E * E * E;
-  const double dx = 1.0 / ((double)(1 << level) * p);
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     const int ix = (int)(i % E) - hw, iy = (int)((i / E) % E) - hw, iz = (int)(i / ((long)E * E)) - hw;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-    if (ix | iy | iz) green::eval(gs, ix * dx, iy * dx, iz * dx, v);
+    if (ix | iy | iz) table_value(gs, mesh, N, level, p, ix, iy, iz, v);
     add_correction(v, ix, iy, iz, level, p, mlp, fp32);
     add_grid(v, ix, iy, iz, level, p, grid);
     uint32_t w[4];
@@ -174,18 +195,18 @@ cudaError_t launch_grid_grad(Plan& P, float* grad, cudaStream_t s) {
 
 cudaError_t launch_tab_bf16(Plan& P, int level, cudaStream_t s) {
   k_tab_bf16<<<4 * P.num_sms, 256, 0, s>>>(P.tab_bf[level], P.p, level, mlp_of(P), P.corr_fp32, grid_of(P, level),
-                                           spec_of(P));
+                                           spec_of(P), P.gmesh, P.N);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tables(Plan& P, cudaStream_t s) {
   for (int l = 2; l <= P.L; ++l) {
     k_tab_m2l<<<4 * P.num_sms, 256, 0, s>>>(P.tab[l], P.tab_lo[l], P.p, l, mlp_of(P), P.corr_fp32, grid_of(P, l),
-                                            spec_of(P));
+                                            spec_of(P), P.gmesh, P.N);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  k_tab_near<<<P.num_sms, 256, 0, s>>>(P.near_tab, P.S, P.N, spec_of(P));
+  k_tab_near<<<P.num_sms, 256, 0, s>>>(P.near_tab, P.S, P.N, spec_of(P), P.gmesh);
   return cudaGetLastError();
 }
 

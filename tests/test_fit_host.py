@@ -19,3 +19,16 @@ def test_simplex_on_rosenbrock_and_in_one_dimension():
     # one parameter (the a_1 fit): a non-smooth (L_MAX-like) objective too
     x, fx, _ = fit.nelder_mead(lambda a: abs(a[0] + 0.12) + 1.0, [-0.125], 0.01, xtol=1e-9, ftol=0.0)
     assert abs(x[0] + 0.12) < 1e-8
+
+
+def test_gk_mesh_helper_equals_the_explicit_inverse_dft():
+    # the G_K mesh handed to fmm_plan_set_green_mesh (FFT on the host here)
+    # against the oracle's explicit inverse-DFT sum of eq. gfk
+    import torch
+    from oracle import pm
+    from paper_2011_07099_gb300 import ablation
+    N = 8
+    K = ablation.g_k_mesh(N, torch.device("cpu")).numpy().reshape(4, N, N, N)
+    kern, grad = pm.g_k_real_space(N)
+    np.testing.assert_allclose(K[0], kern, atol=1e-13)
+    np.testing.assert_allclose(K[1:], -np.moveaxis(grad, -1, 0), atol=1e-13)
