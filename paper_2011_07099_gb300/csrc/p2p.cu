@@ -174,9 +174,19 @@ k_p2p(const float* __restrict__ rho, const double* __restrict__ mean, int N, int
           for (int f = 0; f < 4; ++f)
 #pragma unroll
             for (int x = 0; x < S; ++x) rw[f][x] = 0.f;
+          // 16-byte aligned rows (S % 4 == 0: W and the buffers are multiples
+          // of 4 floats): the masses come in as float4, four at a time
+          float mq[4];
 #pragma unroll
           for (int xp = 0; xp < W; ++xp) {
-            const float m = mrow[xp];
+            if (S % 4 == 0 && xp % 4 == 0) {
+              const float4 q4 = *reinterpret_cast<const float4*>(mrow + xp);
+              mq[0] = q4.x;
+              mq[1] = q4.y;
+              mq[2] = q4.z;
+              mq[3] = q4.w;
+            }
+            const float m = S % 4 == 0 ? mq[xp % 4] : mrow[xp];
 #pragma unroll
             for (int x = 0; x < S; ++x) {
               const int dx = x + S - xp;                    // compile-time after unrolling

@@ -51,6 +51,30 @@ def pm_target(density, N):
     return outs[0].float().contiguous(), torch.stack(outs[1:]).float().contiguous()
 
 
+def pm_target_gk(density, N):
+    """PM with the exact-in-Fourier-space G_K (Sec. 1, eq. gfk): spectral
+    solve of lap Phi = m on the mesh, g = -grad Phi spectrally (the Nyquist
+    derivative zeroed), FP64 FFTs.  Returns (phi, acc) like pm_target."""
+    import torch
+    m = density.double()
+    m = (m - m.mean()) / float(N) ** 3
+    f = torch.fft.fftfreq(N, d=1.0 / N, dtype=torch.float64, device=density.device)
+    fz = torch.fft.rfftfreq(N, d=1.0 / N, dtype=torch.float64, device=density.device)
+    kz, ky, kx = torch.meshgrid(f, f, fz, indexing="ij")
+    k2 = (2 * np.pi) ** 2 * (kx * kx + ky * ky + kz * kz)
+    gt = torch.where(k2 > 0, -1.0 / torch.where(k2 > 0, k2, torch.ones_like(k2)), torch.zeros_like(k2))
+    phih = torch.fft.rfftn(m) * gt * float(N) ** 3
+    phi = torch.fft.irfftn(phih, s=(N, N, N))
+    nyq = N // 2 if N % 2 == 0 else None
+    derivs = []
+    for k in (kx, ky, kz):
+        kk = k.clone()
+        if nyq is not None:
+            kk[kk.abs() == nyq] = 0.0
+        derivs.append(torch.fft.irfftn(-2j * np.pi * kk * phih, s=(N, N, N)))
+    return phi.float().contiguous(), torch.stack(derivs).float().contiguous()
+
+
 def init_weights(seed):
     """Hidden layers ~ N(0, 1/fan_in), biases 0, output layer 0: the initial
     correction is exactly zero (the plain G_S1 table)."""
@@ -100,11 +124,12 @@ class Trainer:
         else:
             B.fmm_plan_set_table_grid(self.plan.handle, self.w)
 
-    def prepare(self, density_np):
-        """Device density, PM target and the relative-error weights of a field."""
+    def prepare(self, density_np, target="gs1"):
+        """Device density, PM target (PM with G_S1, or with G_K for
+        target="gk") and the relative-error weights of a field."""
         import torch
         d = torch.from_numpy(np.ascontiguousarray(density_np, dtype=np.float32)).to(self.device)
-        tphi, tacc = pm_target(d, self.N)
+        tphi, tacc = (pm_target_gk if target == "gk" else pm_target)(d, self.N)
         w_phi = 1.0 / float((tphi.double() ** 2).sum())
         w_g = 1.0 / float((tacc.double() ** 2).sum())
         return d, tphi, tacc, w_phi, w_g
@@ -161,11 +186,14 @@ def main():
     ap.add_argument("--out", default="correction.npz")
     ap.add_argument("--resume", default=None)
     ap.add_argument("--model", choices=["mlp", "grid"], default="mlp")
+    ap.add_argument("--target", choices=["gs1", "gk"], default="gs1",
+                    help="PM reference of the loss: with G_S1 (the paper's G_* definition) or with G_K")
     args = ap.parse_args()
     tr = Trainer(args.n, args.L, args.p, seed=args.seed, lr=args.lr, model=args.model)
     if args.resume:
         tr.load(args.resume)
-    fields = [tr.prepare(inputs.lognormal(args.n, sigma=0.5, seed=args.seed + i)) for i in range(args.fields)]
+    fields = [tr.prepare(inputs.lognormal(args.n, sigma=0.5, seed=args.seed + i), args.target)
+              for i in range(args.fields)]
     t0 = time.time()
     for s in range(tr.step_count, args.steps):
         i0 = (s * args.batch) % len(fields)
