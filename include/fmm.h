@@ -160,6 +160,20 @@ int fmm_plan_set_green_mesh(fmm_plan* plan, const double* mesh, size_t n);
  * each M^3 with x fastest.  Enqueued on `stream`. */
 int fmm_plan_mesh_green(const fmm_plan* plan, double* out, void* stream);
 
+/* How M2L evaluates eq. fmm2 at the fine levels.  FMM_M2L_DENSE (default):
+ * the dense contraction per offset (CUDA cores or, in the mixed forms, the
+ * tensor cores).  FMM_M2L_FFT: the HPM form of Sec. 2, as an ablation: per
+ * parent, the gridlet masses of its neighbours' children on a zero-padded
+ * (8 order)^3 grid, one FFT convolution with the level table (cuFFT, FP32),
+ * and the 27 near nodes' terms subtracted by direct sums; used at the levels
+ * whose local fields are FP32 (the extended-precision coarse levels keep the
+ * dense kernels) of periodic plans, whatever the precision mode.  Allocates
+ * the FFT plans, buffers and table spectra (synchronous; about 7 parents x
+ * (8 order)^3 x 16 bytes per level).  FMM_ERR_ARG for an unknown value. */
+#define FMM_M2L_DENSE 0
+#define FMM_M2L_FFT   1
+int fmm_plan_set_m2l_algorithm(fmm_plan* plan, int algorithm);
+
 /* Limit of every bounded device-side wait (pipeline barriers of the
  * tensor-core M2L), in milliseconds, 1..600000; default 2000.  A wait that
  * runs out makes its kernel skip the rest of its work, wait (bounded) for the

@@ -69,6 +69,42 @@ def fmm_vs_pm(N, L, p, density, green):
             "abs_g": (float(mag.max()), float(mag.pow(2).mean().sqrt()))}
 
 
+def m2l_forms(N, L, p, density, steps=5):
+    """Per-solve time of the M2L stage (CUDA events, median of `steps` after
+    one warm-up) for the dense FP32 form, the dense bf16x3 tensor-core form
+    and the FFT form of the interaction zone (Sec. 2), with each form's
+    relative L2 difference from the dense FP32 solve."""
+    import statistics
+    import torch
+    out = {}
+    ref = None
+    for name, prec, alg in (("dense_fp32", B.FMM_PREC_FP32, B.FMM_M2L_DENSE),
+                            ("dense_bf16x3", B.FMM_PREC_BF16X3, B.FMM_M2L_DENSE),
+                            ("fft_fp32", B.FMM_PREC_FP32, B.FMM_M2L_FFT)):
+        plan = B.Plan(N, L, p)
+        if prec != B.FMM_PREC_FP32:
+            plan.set_precision(prec)
+        B.fmm_plan_set_m2l_algorithm(plan.handle, alg)
+        phi, acc = plan.solve(density)
+        B.fmm_plan_set_timing(plan.handle, True)
+        m2l, lev = [], []
+        for _ in range(steps):
+            plan.solve(density, phi, acc)
+            t = B.fmm_plan_stage_times(plan.handle)
+            m2l.append(t[B.FMM_TIME_M2L])
+            lev.append([t[B.FMM_TIME_M2L_LEVEL0 + l] for l in range(2, L + 1)])
+        torch.cuda.synchronize()
+        B.fmm_plan_check(plan.handle)
+        if ref is None:
+            ref = (phi.clone(), acc.clone())
+        out[name] = {"m2l_ms": statistics.median(m2l),
+                     "level_ms": [statistics.median(x[i] for x in lev) for i in range(L - 1)],
+                     "rel_phi_vs_dense_fp32": float((phi - ref[0]).norm() / ref[0].norm()),
+                     "rel_g_vs_dense_fp32": float((acc - ref[1]).norm() / ref[1].norm())}
+        plan.close()
+    return out
+
+
 def main():
     import argparse
     import json
@@ -78,7 +114,13 @@ def main():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--L", type=int, default=3)
     ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--m2l", action="store_true", help="time the dense and FFT forms of M2L instead")
     args = ap.parse_args()
+    if args.m2l:
+        from . import inputs
+        d = torch.from_numpy(inputs.lognormal(args.n, sigma=0.5, seed=5000)).cuda()
+        print(json.dumps({"N": args.n, "L": args.L, "p": args.p, **m2l_forms(args.n, args.L, args.p, d)}), flush=True)
+        return
     d = torch.from_numpy(accuracy.point_sources(args.n, "corner")).cuda()
     for g in ("S1", "X", "K"):
         print(json.dumps({"N": args.n, "L": args.L, "p": args.p, "green": g, **fmm_vs_pm(args.n, args.L, args.p, d, g)}),

@@ -63,7 +63,7 @@ def build(verbose=False, extra_flags=()):
         raise RuntimeError("nvcc failed for: " + ", ".join(os.path.basename(f) for f in failed))
     objs = [os.path.join(OUT, os.path.basename(s)[:-3] + ".o") for s in srcs]
     if jobs or not os.path.exists(LIB):
-        cmd = [exe, "-shared", "-o", LIB] + objs + ARCH
+        cmd = [exe, "-shared", "-o", LIB] + objs + ARCH + ["-lcufft"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)

@@ -132,6 +132,7 @@ void free_plan(Plan* P) {
   cudaFree(P->grad_partials);
   cudaFree(P->grid);
   cudaFree(P->gmesh);
+  fmm::free_fft(*P);
   for (int l = 0; l <= fmm::kMaxLevel; ++l) cudaFree(P->lam[l]);
   for (int l = 0; l <= fmm::kMaxLevel; ++l) {
     cudaFree(P->tab_bf[l]);
@@ -157,6 +158,14 @@ bool dev_alloc(T** ptr, size_t count) {
 // grid), synchronously.  Returns an FMM_* code.
 int retabulate(Plan& P) {
   if (fmm::launch_tables(P, 0) != cudaSuccess) return FMM_ERR_CUDA;
+  if (P.fft) {   // the FFT form keeps the tables' spectra: rebuild them
+    fmm::free_fft(P);
+    if (P.m2l_fft) {
+      if (cudaDeviceSynchronize() != cudaSuccess) return FMM_ERR_CUDA;
+      const int rc = fmm::prepare_fft(P);
+      if (rc != FMM_OK) return rc;
+    }
+  }
   if (P.tc_ready) {
     for (int l = fmm::kTcMinLevel; l <= P.L; ++l) {
       if (!P.Apre[l]) continue;
@@ -254,7 +263,8 @@ fmm_plan* fmm_plan_create(int N, int L, int order) {
     ok = dev_alloc(&P->M[l], nodes * p3) && dev_alloc(&P->F[l], nodes * 4 * p3) &&
          dev_alloc(&P->tab[l], E * E * E);
     // split tables for the coarse levels, and for every wide level of the high orders
-    if (ok && (l <= fmm::kExtTopLevel || (p >= fmm::kWideOrder && l < L))) ok = dev_alloc(&P->tab_lo[l], E * E * E);
+    if (ok && (l <= fmm::kExtTopLevel || (p >= fmm::kWideOrder && l < L) || S >= fmm::kWideLeaf))
+      ok = dev_alloc(&P->tab_lo[l], E * E * E);
     // FP64 gridlet masses at every level at high order (the leaf copy feeds M2M:
     // the coarse far-field sums cancel ~1000-fold there, so FP32 rounding of
     // the leaf masses alone would cost ~1e-6)
@@ -357,7 +367,8 @@ int prepare_tc(Plan& P) {
     if (P.Apre[l]) continue;
     const size_t nodes = (size_t)1 << (3 * l);
     if ((!P.tab_bf[l] && !dev_alloc(&P.tab_bf[l], E * E * E)) ||
-        (!P.Mbf_hi[l] && cudaMalloc(&P.Mbf_hi[l], nodes * kp * 2 * 2) != cudaSuccess) ||
+        (!P.Mbf_hi[l] && (cudaMalloc(&P.Mbf_hi[l], (nodes + 1) * kp * 2 * 2) != cudaSuccess ||
+                          cudaMemset(P.Mbf_hi[l], 0, (nodes + 1) * kp * 2 * 2) != cudaSuccess)) ||
         cudaMalloc(&P.Apre[l], fmm::tc_apre_bytes(P.p)) != cudaSuccess)
       return FMM_ERR_ALLOC;
     if (fmm::launch_tab_bf16(P, l, 0) != cudaSuccess || fmm::launch_build_a(P, l, 0) != cudaSuccess)
@@ -444,6 +455,21 @@ int fmm_plan_set_green_mesh(fmm_plan* plan, const double* mesh, size_t n) {
   g.kind = 4;
   P.gspec = g;
   return set_err(retabulate(P));
+}
+
+int fmm_plan_set_m2l_algorithm(fmm_plan* plan, int algorithm) {
+  if (!plan || (algorithm != FMM_M2L_DENSE && algorithm != FMM_M2L_FFT)) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  P.m2l_fft = algorithm == FMM_M2L_FFT ? 1 : 0;
+  if (P.m2l_fft) {
+    const int rc = fmm::prepare_fft(P);
+    if (rc != FMM_OK) {
+      fmm::free_fft(P);
+      P.m2l_fft = 0;
+      return set_err(rc);
+    }
+  }
+  return set_err(FMM_OK);
 }
 
 int fmm_plan_set_timeout_ms(fmm_plan* plan, int ms) {
@@ -625,7 +651,9 @@ int fmm_solve(fmm_plan* plan, const float* density, float* potential, float* acc
   const bool tc = P.prec != FMM_PREC_FP32 && P.tc_ready;
   for (int l = 2; l <= P.L; ++l) {
     FMM_CUDA_TRY(mark(FMM_TIME_M2L_LEVEL0 + l, 0));
-    if (tc && l >= fmm::tc_first_level(P)) {
+    if (fmm::fft_level(P, l)) {
+      FMM_CUDA_TRY(fmm::launch_m2l_fft(P, l, s));
+    } else if (tc && l >= fmm::tc_first_level(P)) {
       FMM_CUDA_TRY(fmm::launch_split_bf16(P, l, s));
       FMM_CUDA_TRY(fmm::launch_m2l_tc(P, l, P.prec, s));
     } else {

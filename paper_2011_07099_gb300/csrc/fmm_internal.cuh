@@ -96,10 +96,13 @@ struct Plan {
   int8_t* offsets[kMaxLevel + 1] = {};  // per level: [8 child types][n_off][3] (dx, dy, dz) = T - S
   // tensor-core M2L (levels >= kTcMinLevel, allocated on the first mixed-precision solve)
   uint4* tab_bf[kMaxLevel + 1] = {};       // per table entry, per field: bf16 hi | bf16 lo << 16
-  void* Mbf_hi[kMaxLevel + 1] = {};        // gridlet masses split into bf16 hi / lo (interleaved per 8), rows padded
+  void* Mbf_hi[kMaxLevel + 1] = {};        // gridlet masses split into bf16 hi / lo (interleaved per 8), rows padded;
+                                           // one extra all-zero node after the 8^l nodes (gather target of empty slots)
   void* Mbf_lo[kMaxLevel + 1] = {};        // unused (kept null)
   void* Apre[kMaxLevel + 1] = {};          // precomputed split translation tiles per offset slot
   int tc_group = 4;                        // offsets accumulated per TMEM partial before promotion
+  int m2l_fft = 0;                         // FFT form of the interaction zone at the fine levels (ablation)
+  void* fft = nullptr;                     // its cuFFT plans and buffers (m2l_fft.cu)
   int tc_min_level = kTcMinLevel;          // first level on the tensor cores in the mixed forms
   // learned table correction (MLP weights) and its training buffers
   float* corr_w = nullptr;                 // mlp::kParams weights (device) or unset
@@ -136,11 +139,19 @@ struct Plan {
 // plan creation, never inside a solve, so a solve is safe to capture.
 cudaError_t setup_upward(const Plan& P);
 // Levels whose local field is kept in FP64 (M2L output reduced in FP64, L2L
-// from them in double-float): the two coarse levels, and at high order every level
-// above the leaves.
-inline bool wide_level(const Plan& P, int l) { return l <= kExtTopLevel || (P.p >= kWideOrder && l < P.L); }
-// First level of the tensor-core M2L in the mixed forms.
+// from them in double-float): the two coarse levels, at high order every level
+// above the leaves, and with 16-cell leaves every level: the L2P of a 16-cell
+// leaf extrapolates far beyond the gridlet (absolute weight sums up to 835 at
+// p = 6), which amplifies the FP32 rounding of the leaf field at the leaf's
+// edge cells to ~1e-7 of the potential, so that leaf field stays FP64.
+constexpr int kWideLeaf = 16;
+inline bool wide_level(const Plan& P, int l) {
+  return l <= kExtTopLevel || (P.p >= kWideOrder && l < P.L) || P.S >= kWideLeaf;
+}
+// First level of the tensor-core M2L in the mixed forms (above L: none; the
+// tensor-core kernel writes FP32 fields only, so 16-cell leaves do not use it).
 inline int tc_first_level(const Plan& P) {
+  if (P.S >= kWideLeaf) return P.L + 1;
   return P.p >= kWideOrder ? (P.tc_min_level > P.L ? P.tc_min_level : P.L) : P.tc_min_level;
 }
 
@@ -159,6 +170,14 @@ cudaError_t launch_mean_into(const Plan& P, const float* rho, double* partials, 
 cudaError_t launch_p2m(Plan& P, const float* rho, cudaStream_t s);
 cudaError_t launch_m2m(Plan& P, int level, cudaStream_t s);       // level+1 -> level
 cudaError_t launch_m2l_fp32(Plan& P, int level, cudaStream_t s);  // writes F[level] (and F64[level] when coarse)
+// FP32 M2L over one offset list for all child types, written into F[level].
+cudaError_t launch_m2l_fp32_list(Plan& P, int level, const int8_t* offs, int n_off, cudaStream_t s);
+// The FFT form of the interaction zone (m2l_fft.cu): levels that use it,
+// set-up of plans/buffers/table spectra (FMM_* code), launch, release.
+bool fft_level(const Plan& P, int level);
+int prepare_fft(Plan& P);
+cudaError_t launch_m2l_fft(Plan& P, int level, cudaStream_t s);
+void free_fft(Plan& P);
 cudaError_t launch_l2l(Plan& P, int level, cudaStream_t s);       // F[level] -> F[level+1] (adds)
 cudaError_t launch_p2p(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s);
 cudaError_t setup_m2l_tc(const Plan& P);

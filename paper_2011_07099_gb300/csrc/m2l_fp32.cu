@@ -399,7 +399,10 @@ cudaError_t launch_p(Plan& Pl, int level, cudaStream_t s) {
   float* out = wide ? Pl.m2l_part : Pl.F[level];
   dim3 grid((n_par + NT - 1) / NT, 8, nsplit);
   const double* m64 = wide ? Pl.M64[level] : nullptr;   // FP64 masses: wide levels of the high orders
-  if (level == 2 || m64)   // double-float sums: level 2, and every wide level of the high orders
+  // double-float sums: level 2, every wide level of the high orders, and
+  // every level with 16-cell leaves (whose L2P amplifies the rounding of the
+  // sums that varies from one gridlet point to the next)
+  if (level == 2 || m64 || Pl.S >= kWideLeaf)
     k_m2l_df<P><<<grid, threads, sizeof(float4) * (2 * D * D * D + 2 * P3 * (NT / 4)), s>>>(
         Pl.M[level], out, Pl.tab[level], Pl.tab_lo[level], Pl.offsets[level], n_off, level, per, field, 1, m64,
         Pl.iso);
@@ -415,6 +418,20 @@ cudaError_t launch_p(Plan& Pl, int level, cudaStream_t s) {
     k_m2l_fp32<P, 0><<<grid, threads, smem, s>>>(Pl.M[level], out, Pl.tab[level], nullptr, Pl.offsets[level],
                                                  n_off, level, per, field, wide ? 1 : 0, nullptr, Pl.iso);
   if (wide) k_sum_ranges<<<4 * Pl.num_sms, 256, 0, s>>>(Pl.m2l_part, nsplit, field, Pl.F64[level], Pl.F[level]);
+  return cudaGetLastError();
+}
+
+// FP32 M2L over a caller's offset list (same list for the 8 child types),
+// written straight into F[level]: the near-node part that the FFT form of
+// the interaction zone subtracts (m2l_fft.cu).
+template <int P>
+cudaError_t launch_list_p(Plan& Pl, int level, const int8_t* offs, int n_off, cudaStream_t s) {
+  constexpr int P3 = P * P * P, D = 2 * P - 1, NT = M2LShape<P>::NT;
+  const size_t smem = sizeof(float4) * (D * D * D + P3 * (NT / 4));
+  const uint32_t n_par = 1u << (3 * (level - 1));
+  dim3 grid((n_par + NT - 1) / NT, 8, 1);
+  k_m2l_fp32<P, 0><<<grid, M2LShape<P>::THREADS, smem, s>>>(Pl.M[level], Pl.F[level], Pl.tab[level], nullptr, offs,
+                                                            n_off, level, n_off, 0, 0, nullptr, Pl.iso);
   return cudaGetLastError();
 }
 
@@ -465,6 +482,20 @@ cudaError_t setup_m2l_fp32(const Plan& P) {
     case 6: return setup_p<6>();
     case 7: return setup_p<7>();
     case 8: return setup_p<8>();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_m2l_fp32_list(Plan& P, int level, const int8_t* offs, int n_off, cudaStream_t s) {
+  switch (P.p) {
+    case 1: return launch_list_p<1>(P, level, offs, n_off, s);
+    case 2: return launch_list_p<2>(P, level, offs, n_off, s);
+    case 3: return launch_list_p<3>(P, level, offs, n_off, s);
+    case 4: return launch_list_p<4>(P, level, offs, n_off, s);
+    case 5: return launch_list_p<5>(P, level, offs, n_off, s);
+    case 6: return launch_list_p<6>(P, level, offs, n_off, s);
+    case 7: return launch_list_p<7>(P, level, offs, n_off, s);
+    case 8: return launch_list_p<8>(P, level, offs, n_off, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -194,7 +194,7 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
 #pragma unroll
       for (int h = 0; h < kNT / kProd; ++h) {
         const int t = pt + h * kProd;
-        int key = -1;
+        int key = 1 << (3 * level);   // no source: the all-zero node after the 8^l nodes
         if (par0 + t < n_par) {
           uint32_t x, y, z;
           unmorton(8u * (par0 + t) + ctype, x, y, z);
@@ -226,10 +226,12 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
         for (int pass = 0; pass < kNT / 16; ++pass) {
           const int t = (pt >> 3) + 16 * pass;
           if (MODE == 3 || split == 0) {
+            // full 16-byte reads only (no zero-fill operand): lanes then merge
+            // into whole-sector requests; empty slots read the zero node
             const int key = sk[t];
-            const size_t e0 = ((size_t)(key < 0 ? 0 : key) * (KP / 8) + ch * (kKC / 8) + c8) * 16 + split * 8;
+            const size_t e0 = ((size_t)key * (KP / 8) + ch * (kKC / 8) + c8) * 16 + split * 8;
             const uint32_t d = sB + split * kTileB + (uint32_t)((c8 * (kNT / 8) + t / 8) * 128 + (t % 8) * 16);
-            tc::cp_async16(d, Msp + e0, key < 0 ? 0u : 16u);
+            tc::cp_async16_full(d, Msp + e0);
           }
         }
         tc::cp_async_arrive_noinc(&full[st]);

@@ -255,10 +255,11 @@ k_p2p(const float* __restrict__ rho, const double* __restrict__ mean, int N, int
 // chunk; the sign of dx is the same for the whole chunk except in the
 // target's own chunk (base 0), where it is resolved at compile time.  The
 // summation keeps the row -> plane -> total partial sums of the kernel above.
-// L2P runs in double-float here: the cells at the edges of a 16-cell leaf lie
-// well outside the order-p gridlet's hull (absolute weight sums up to 835 at
-// p = 6 against 46 for 8-cell leaves), which amplifies the rounding of FP32
-// partial sums to ~1e-5 of the potential at the leaf corners.
+// L2P runs in double-float from the leaf's FP64 local field (every level is
+// wide with 16-cell leaves, fmm_internal.cuh): the cells at the edges of a
+// 16-cell leaf lie well outside the order-p gridlet's hull (absolute weight
+// sums up to 835 at p = 6 against 46 for 8-cell leaves), which amplifies any
+// FP32 rounding of the field or of the partial sums at the leaf's edges.
 constexpr int kS16 = 16, kW16 = 48, kT16 = 256;
 
 struct P2P16Smem {
@@ -294,7 +295,7 @@ __device__ __forceinline__ void p2p16_chunk(float rw[4][8], const float4 t[15], 
 
 __global__ void __launch_bounds__(kT16, 1)
 k_p2p16(const float* __restrict__ rho, const double* __restrict__ mean, int N, int L, int p,
-        const float4* __restrict__ near_tab, const float* __restrict__ Fleaf, const float2* __restrict__ wp2m,
+        const float4* __restrict__ near_tab, const double* __restrict__ Fleaf, const float2* __restrict__ wp2m,
         float* __restrict__ phi, float* __restrict__ acc_out, int vec, int iso) {
   extern __shared__ float4 sm4[];
   float* base = reinterpret_cast<float*>(sm4);
@@ -347,7 +348,7 @@ k_p2p16(const float* __restrict__ rho, const double* __restrict__ mean, int N, i
     float2* o2 = reinterpret_cast<float2*>(base + lay.o2);
     constexpr int S3 = kS16 * kS16 * kS16;
     for (int f = 0; f < 4; ++f) {
-      for (int i = tid; i < p3; i += nthr) in2[i] = make_float2(Fleaf[((size_t)leaf * 4 + f) * p3 + i], 0.f);
+      for (int i = tid; i < p3; i += nthr) in2[i] = df_from_double(Fleaf[((size_t)leaf * 4 + f) * p3 + i]);
       __syncthreads();
       contract3_df(in2, reinterpret_cast<float2*>(base + lay.t1), reinterpret_cast<float2*>(base + lay.t2), o2, p,
                    kS16, W8, kS16, true, tid, nthr);      // ends with a barrier
@@ -442,7 +443,7 @@ cudaError_t launch_s16(Plan& P, const float* rho, float* phi, float* acc, cudaSt
   const size_t smem = sizeof(float) * (size_t)P2P16Smem(P.p).total;
   const unsigned leaves = 1u << (3 * P.L);
   const int vec = (reinterpret_cast<uintptr_t>(rho) & 15u) == 0;
-  k_p2p16<<<2 * leaves, kT16, smem, s>>>(rho, P.d_mean, P.N, P.L, P.p, P.near_tab, P.F[P.L], P.w_p2m, phi, acc, vec,
+  k_p2p16<<<2 * leaves, kT16, smem, s>>>(rho, P.d_mean, P.N, P.L, P.p, P.near_tab, P.F64[P.L], P.w_p2m, phi, acc, vec,
                                         P.iso);
   return cudaGetLastError();
 }

@@ -112,14 +112,14 @@ class AnsatzObjective:
         self.plan.close()
 
 
-def fit(N, L, p, density, n_terms=1, norm="l2", gerr=False, x0=None, step=0.01, xtol=1e-5):
+def fit(N, L, p, density, n_terms=1, norm="l2", gerr=False, x0=None, step=0.01, xtol=1e-5, ftol=1e-9):
     """Best-fit a_1..a_n (starting at a_1 = -1/8, the G_S1 value) and the
     error norm there.  Returns {"a": [...], "norm": value, "evaluations": k,
     "at_gs1": the norm at a_1 = -1/8}."""
     obj = AnsatzObjective(N, L, p, density, norm=norm, gerr=gerr)
     start = np.array(x0 if x0 is not None else [-0.125] + [0.0] * (n_terms - 1), dtype=np.float64)
     at_gs1 = obj(np.array([-0.125] + [0.0] * (n_terms - 1)))
-    x, fx, ev = nelder_mead(obj, start, step, xtol=xtol, ftol=0.0)
+    x, fx, ev = nelder_mead(obj, start, step, xtol=xtol, ftol=ftol * at_gs1)
     obj.close()
     return {"a": [float(v) for v in x], "norm": fx, "evaluations": ev, "at_gs1": at_gs1}
 

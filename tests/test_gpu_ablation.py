@@ -23,7 +23,7 @@ def B():
 
 
 def test_gx_tabulation_matches_oracle(B):
-    N = 20
+    N = 24
     plan = B.Plan(N, 2, 5)
     B.fmm_plan_set_green(plan.handle, B.FMM_GREEN_X)
     K = torch.empty(4 * N ** 3, dtype=torch.float64, device="cuda")

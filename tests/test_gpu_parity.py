@@ -64,6 +64,8 @@ CASES = [
     (32, 5, 2, "lognormal"),   # the 32^3 5-level p = 2 workload, S = 1
     (64, 3, 6, "lognormal"),   # S = 8, p = 6: several M2L tiles and a ragged last tile
     (64, 4, 3, "plummer"),     # S = 4, odd order
+    (32, 3, 6, "lognormal"),   # S = 4 below p = 6: the shape of the batch workload's small order-6 fields
+    (48, 3, 6, "plummer"),     # S = 6 = p, N = 48 (a batch size that needs S = 3 or 6)
 ]
 
 
