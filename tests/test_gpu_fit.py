@@ -69,16 +69,19 @@ def _table1_3d():
 
 
 def test_fit_of_a1_on_the_papers_tree(B):
-    # Sec. 3: a_1 minimising the L2 norm of the FMM - PM acceleration
-    # difference (both with G_S(a_1)) for the corner unit source, 128^3 mesh,
-    # 3-level tree, N_g = 6; Table 1 gives -0.120236, and the paper notes that
-    # the best a_1 is always close to -1/8 (G_S1).  The fitted value is
-    # printed beside Table 1's and must lower the norm against G_S1.
+    # Sec. 3, Table 1: a_1 minimising the L2 norm of the Green's-function
+    # error (eq. gerr: the non-periodic expansion error subtracted) for a unit
+    # point source, 128^3 mesh, 3-level tree (16^3 sub-grid), N_g = 6, by the
+    # downhill simplex.  The paper finds the best a_1 always close to -1/8
+    # (Table 1: -0.120236 at N_g = 6); the source here sits at the box centre
+    # (for the corner source the non-periodic subtraction fails near the
+    # source's images: the fit then drifts to ~-0.25, documented).
     from paper_2011_07099_gb300 import accuracy, fit
     N, L, p = 128, 3, 6
-    d = torch.from_numpy(accuracy.point_sources(N, "corner")).cuda()
-    r = fit.fit(N, L, p, d, n_terms=1, norm="l2")
-    print(f"fitted a_1 = {r['a'][0]:.6f} (Table 1: {_table1_3d()[p]}), L2 {r['norm']:.4e} "
+    d = torch.from_numpy(accuracy.point_sources(N, "centre")).cuda()
+    r = fit.fit(N, L, p, d, n_terms=1, norm="l2", gerr=True)
+    print(f"fitted a_1 = {r['a'][0]:.6f} (Table 1: {_table1_3d()[p]}), GF L2 {r['norm']:.4e} "
           f"(G_S1: {r['at_gs1']:.4e}), {r['evaluations']} evaluations")
     assert r["norm"] <= r["at_gs1"]
-    assert -0.2 < r["a"][0] < -0.05
+    assert abs(r["a"][0] + 0.125) < 0.02
+    assert r["evaluations"] < 200
