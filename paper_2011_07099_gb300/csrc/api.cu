@@ -9,6 +9,8 @@
 #include <tuple>
 #include <vector>
 
+#include <cuda.h>
+
 #include "fmm_internal.cuh"
 #include "mlp.cuh"
 
@@ -139,6 +141,7 @@ void free_plan(Plan* P) {
     cudaFree(P->Mbf_hi[l]);
     cudaFree(P->Mbf_lo[l]);
     cudaFree(P->Apre[l]);
+    delete static_cast<CUtensorMap*>(P->tmapB[l]);
   }
   cudaFree(P->w_p2m);
   cudaFree(P->w_m2m);
@@ -361,18 +364,17 @@ namespace {
 // (levels that already have them are kept).  Tabulated once, synchronously.
 int prepare_tc(Plan& P) {
   const size_t E = 8 * P.p - 1;
-  const size_t kp = (size_t)fmm::tc_padded_k(P.p);
   bool made = false;
   for (int l = fmm::tc_first_level(P); l <= P.L; ++l) {
     if (P.Apre[l]) continue;
-    const size_t nodes = (size_t)1 << (3 * l);
     if ((!P.tab_bf[l] && !dev_alloc(&P.tab_bf[l], E * E * E)) ||
-        (!P.Mbf_hi[l] && (cudaMalloc(&P.Mbf_hi[l], (nodes + 1) * kp * 2 * 2) != cudaSuccess ||
-                          cudaMemset(P.Mbf_hi[l], 0, (nodes + 1) * kp * 2 * 2) != cudaSuccess)) ||
+        (!P.Mbf_hi[l] && cudaMalloc(&P.Mbf_hi[l], fmm::tc_bsplit_bytes(P.p, l)) != cudaSuccess) ||
         cudaMalloc(&P.Apre[l], fmm::tc_apre_bytes(P.p)) != cudaSuccess)
       return FMM_ERR_ALLOC;
     if (fmm::launch_tab_bf16(P, l, 0) != cudaSuccess || fmm::launch_build_a(P, l, 0) != cudaSuccess)
       return FMM_ERR_CUDA;
+    const int rc = fmm::make_tc_map(P, l);
+    if (rc != FMM_OK) return rc;
     made = true;
   }
   if (made && cudaDeviceSynchronize() != cudaSuccess) return FMM_ERR_CUDA;

@@ -96,8 +96,9 @@ struct Plan {
   int8_t* offsets[kMaxLevel + 1] = {};  // per level: [8 child types][n_off][3] (dx, dy, dz) = T - S
   // tensor-core M2L (levels >= kTcMinLevel, allocated on the first mixed-precision solve)
   uint4* tab_bf[kMaxLevel + 1] = {};       // per table entry, per field: bf16 hi | bf16 lo << 16
-  void* Mbf_hi[kMaxLevel + 1] = {};        // gridlet masses split into bf16 hi / lo (interleaved per 8), rows padded;
-                                           // one extra all-zero node after the 8^l nodes (gather target of empty slots)
+  void* Mbf_hi[kMaxLevel + 1] = {};        // gridlet masses split into bf16 hi / lo, per parity class with a halo
+                                           // (layout in m2l_tc.cu, k_split_bf16), rows padded to KP
+  void* tmapB[kMaxLevel + 1] = {};         // host CUtensorMap of each Mbf_hi level (the tensor loads of B)
   void* Mbf_lo[kMaxLevel + 1] = {};        // unused (kept null)
   void* Apre[kMaxLevel + 1] = {};          // precomputed split translation tiles per offset slot
   int tc_group = 4;                        // offsets accumulated per TMEM partial before promotion
@@ -210,6 +211,9 @@ cudaError_t launch_split_bf16(Plan& P, int level, cudaStream_t s);
 cudaError_t launch_m2l_tc(Plan& P, int level, int mode, cudaStream_t s);
 int tc_padded_k(int p);
 size_t tc_apre_bytes(int p);
+size_t tc_bsplit_bytes(int p, int level);
+// Encodes P.tmapB[level] for P.Mbf_hi[level] (FMM_* code).
+int make_tc_map(Plan& P, int level);
 cudaError_t launch_build_a(Plan& P, int level, cudaStream_t s);
 
 // Block-wide separable contraction over the middle axis of a [A][Kin][B]

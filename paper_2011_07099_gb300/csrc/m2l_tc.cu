@@ -11,19 +11,24 @@
 //
 // The translation operand A_o depends only on the offset (not on the target),
 // so it is built once per plan, split into BF16 hi + lo, in the exact shared-
-// memory tile layout (`k_build_a`), and each pipeline stage streams its two
-// 8 KB tiles with one bulk asynchronous copy.
+// memory tile layout (`k_build_a`); each pipeline stage streams its two 8 KB
+// tiles with bulk asynchronous copies.
+//
+// The source operand B_o: a CTA's 256 targets of child type c are the
+// children of an 8 x 8 x 4 box of parents, so the sources T - o of one offset
+// all have the same parity class and form an 8 x 8 x 4 box in that class.
+// The split multipoles are kept per parity class in spatial order with a
+// 2-node halo (periodic copies, or zeros for the isolated problem), so each
+// stage's B tile (256 targets x 32 reduction indices, per split) is ONE 5-D
+// TMA tensor load, written in the 64-byte-swizzled K-major layout the MMA
+// reads: whole lines from L2, no per-lane gathers.
 //
 // CTA tile: 128 rows of (f, r) x 256 targets (one M = 128, N = 256 MMA per
-// 16-deep k step, so every A byte staged feeds 256 targets).  Warp roles:
+// 16-deep k step).  Warp roles:
 //   warp 0      issues the MMAs (one thread);
-//   warps 1..4  per stage (32 reduction indices of one offset): one thread
-//               arms the stage's A barrier with the A bytes and issues the
-//               bulk copies; all gather B, the source nodes' split BF16
-//               masses, with 16-byte cp.async whose completion arrives on the
-//               stage barrier (hi and lo are interleaved every 8 values, so a
-//               target's stage slice is one 128-byte line);
-//   warps 5..8  drain TMEM: every G offsets accumulate into a fresh TMEM
+//   warp 1      one thread arms each stage's barrier with the stage's bytes
+//               and issues its bulk copies (A) and tensor loads (B);
+//   warps 2..5  drain TMEM: every G offsets accumulate into a fresh TMEM
 //               partial, which the drain warps add into an FP32 total kept in
 //               TMEM while the issuer waits.  A single TMEM accumulator over
 //               all 189 p^3 terms drifts by ~1e-4 on the coherent, cancelling
@@ -31,15 +36,19 @@
 //               per-group partials summed in FP32 with rounding to nearest
 //               cost ~1e-7 (CPU emulation of the level's sums), far below the
 //               bf16x3 operand error.
-// Layout: canonical no-swizzle K-major core matrices (8 rows x 16 B).
-// bf16x3 mode accumulates A_hi B_hi + A_hi B_lo + A_lo B_hi; bf16 mode A_hi B_hi.
+// A tiles: canonical no-swizzle K-major core matrices (8 rows x 16 B); B
+// tiles: 64-byte swizzle, K-major.  bf16x3 mode accumulates A_hi B_hi +
+// A_hi B_lo + A_lo B_hi; bf16 mode A_hi B_hi.
 // TMEM: 512 columns = partial (256) | total (256).
 // Every wait is bounded; a timeout sets the plan's error word and later work
 // is skipped without leaving any barrier sequence.  Before the CTA exits the
 // issuer waits (bounded) for the completion of every MMA it issued and the
-// copy thread for every A copy it issued, so nothing is still in flight into
+// copy thread for every copy it issued, so nothing is still in flight into
 // this CTA's TMEM or shared memory; then TMEM is freed and the kernel returns.
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <new>
 
 #include "fmm_internal.cuh"
 #include "tc_ptx.cuh"
@@ -49,12 +58,14 @@ namespace {
 
 constexpr int kKC = 32;          // reduction indices per pipeline stage
 constexpr int kNT = 256;         // targets per CTA (MMA N)
-constexpr int kProd = 128;       // producer threads (warps 1..4)
-constexpr int kDrain = 128;      // drain threads (warps 5..8)
-constexpr int kThreads = 32 + kProd + kDrain;
+constexpr int kBX = 8, kBY = 8, kBZ = 4;   // the targets' parents: an 8 x 8 x 4 box
+constexpr int kHalo = 2;         // halo of the per-class source arrays (|(c - o - q)/2| <= 2)
+constexpr int kDrain = 128;      // drain threads (warps 2..5)
+constexpr int kThreads = 64 + kDrain;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kTileBytes = 128 * kKC * 2;     // one 128 x 32 BF16 tile of A
 constexpr int kTileB = kNT * kKC * 2;         // one 256 x 32 BF16 tile of B
+static_assert(kBX * kBY * kBZ == kNT, "target box");
 
 template <int P, int MODE>
 struct TcShape {
@@ -64,58 +75,57 @@ struct TcShape {
   static constexpr int MT = (4 * P3 + 127) / 128;            // row tiles
   static constexpr int NSPLIT = MODE == 3 ? 2 : 1;
   static constexpr int STAGE_BYTES = NSPLIT * (kTileBytes + kTileB);
-  static constexpr int EXTRA = 2 * kNT * 4 + 64;
+  static constexpr int EXTRA = 64;
   static constexpr int LIMIT = 225 * 1024;                  // dynamic shared memory budget
-  static constexpr int FIT = (LIMIT - EXTRA) / STAGE_BYTES;
+  static constexpr int FIT = (LIMIT - EXTRA - 1024) / STAGE_BYTES;
   static constexpr int ST = FIT > 6 ? 6 : FIT;              // pipeline depth
   static_assert(FIT >= 3, "pipeline needs at least 3 stages");
-  static constexpr int SMEM = ST * STAGE_BYTES + EXTRA;
+  static constexpr int SMEM = ST * STAGE_BYTES + EXTRA + 1024;   // + alignment slack
 };
 
 // Offsets o with |o_i| <= 3 are indexed ((oz+3) 7 + (oy+3)) 7 + (ox+3).
 __host__ __device__ constexpr int off_index(int ox, int oy, int oz) { return ((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3); }
 constexpr int kOffSlots = 343;
 
-__device__ __forceinline__ void producer_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kProd) : "memory"); }
-
 template <int P, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
-k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre,
+k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ Apre,
          const int8_t* __restrict__ offs, int n_off, int level, int group,
-         float* __restrict__ F, int* __restrict__ err, uint64_t kWaitNs, int stall, int iso) {
+         float* __restrict__ F, int* __restrict__ err, uint64_t kWaitNs, int stall) {
   using Sh = TcShape<P, MODE>;
-  constexpr int P3 = Sh::P3, KP = Sh::KP, NCH = Sh::NCH, MT = Sh::MT, ST = Sh::ST, NSPLIT = Sh::NSPLIT;
+  constexpr int P3 = Sh::P3, NCH = Sh::NCH, MT = Sh::MT, ST = Sh::ST, NSPLIT = Sh::NSPLIT;
   constexpr int STAGE_BYTES = Sh::STAGE_BYTES;
   static_assert(Sh::SMEM <= Sh::LIMIT, "shared-memory budget");
   constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, kNT);
   constexpr uint32_t LBO_A = (128 / 8) * 128;      // next core matrix along K in an A tile
-  constexpr uint32_t LBO_B = (kNT / 8) * 128;      // next core matrix along K in a B tile
-  constexpr uint32_t A_TX = NSPLIT * kTileBytes;
+  constexpr uint32_t SBO_B = 8 * kKC * 2;          // 8 rows of 64 bytes in a B tile
+  constexpr uint32_t TX = NSPLIT * (kTileBytes + kTileB);
 
-  extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* stages = smem;                                                // ST x [A tiles | B tiles]
-  int* srckey = reinterpret_cast<int*>(smem + ST * STAGE_BYTES);         // 2 x kNT
-  // full: the producers' cp.async gathers of B landed; afull: the bulk copy of
-  // A landed (its own barrier, so that a CTA that gives up can still wait for
-  // exactly the copies it issued); empty: the MMAs reading the stage are done;
-  // pfull / pfree: a group's partial is complete / has been added to the total.
-  __shared__ uint64_t full[ST], afull[ST], empty[ST], pfull, pfree, mdone;
+  extern __shared__ uint8_t smem[];
+  // full: the stage's copies landed (A bulk + B tensor, counted in bytes);
+  // empty: the MMAs reading the stage are done; pfull / pfree: a group's
+  // partial is complete / has been added to the total.
+  __shared__ uint64_t full[ST], empty[ST], pfull, pfree, mdone;
   __shared__ uint32_t tmem_holder;
   __shared__ int s_err;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nt = blockIdx.x, mt = blockIdx.y, ctype = blockIdx.z;
-  const int n = 1 << level;
-  const uint32_t n_par = 1u << (3 * (level - 1));
-  const uint32_t par0 = (uint32_t)nt * kNT;
+  const int mt = blockIdx.y, ctype = blockIdx.z;
+  const int nh = 1 << (level - 1);                 // parents per dimension
+  const int tiles_x = nh / kBX, tiles_y = nh / kBY;
+  const int bx = (int)blockIdx.x % tiles_x, by = ((int)blockIdx.x / tiles_x) % tiles_y,
+            bz = (int)blockIdx.x / (tiles_x * tiles_y);
+  const int P0x = bx * kBX, P0y = by * kBY, P0z = bz * kBZ;     // the box of parents
+  const int cx = ctype & 1, cy = (ctype >> 1) & 1, cz = ctype >> 2;
   const int8_t* my_offs = offs + (size_t)ctype * n_off * 3;
   const int n_grp = (n_off + group - 1) / group;
+  // stages at a 1024-byte boundary (the swizzled B tiles need 512)
+  const uint32_t smem_base = (tc::smem_u32(smem) + 1023u) & ~1023u;
 
   if (tid == 0) {
     s_err = 0;
     for (int i = 0; i < ST; ++i) {
-      tc::mbar_init(&full[i], kProd);          // one cp.async-completion arrival per producer thread
-      tc::mbar_init(&afull[i], 1);             // the A expect_tx arrival (+ its bytes)
+      tc::mbar_init(&full[i], 1);              // the expect_tx arrival (+ the stage's bytes)
       tc::mbar_init(&empty[i], 1);             // one MMA completion
     }
     tc::mbar_init(&pfull, 1);
@@ -129,7 +139,6 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
   tc::fence_after_sync();
   const uint32_t tmem = tmem_holder;
   const uint32_t t_tot = tmem + kNT;
-  const uint32_t smem_base = tc::smem_u32(stages);
 
   if (warp == 0) {
     // ------------------------------------------------------------ MMA issuer
@@ -148,23 +157,21 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
         tc::fence_after_sync();
         for (int ch = 0; ch < NCH; ++ch) {
           const int it = io * NCH + ch, st = it % ST;
-          const uint32_t ph = (uint32_t)(it / ST) & 1u;
-          if (!tc::mbar_wait_bounded(&afull[st], ph, kWaitNs) || !tc::mbar_wait_bounded(&full[st], ph, kWaitNs)) {
+          if (!tc::mbar_wait_bounded(&full[st], (uint32_t)(it / ST) & 1u, kWaitNs)) {
             ok = false;
             break;
           }
-          tc::fence_proxy_async_smem();     // cp.async (generic proxy) data -> tensor core
           tc::fence_after_sync();
           const uint32_t sA = smem_base + st * STAGE_BYTES;
           const uint32_t sB = sA + NSPLIT * kTileBytes;
 #pragma unroll
           for (int j = 0; j < kKC / 16; ++j) {
             const uint64_t ah = tc::smem_desc(sA + j * 2 * LBO_A, LBO_A, 128);
-            const uint64_t bh = tc::smem_desc(sB + j * 2 * LBO_B, LBO_B, 128);
+            const uint64_t bh = tc::smem_desc_sw64(sB + j * 32, SBO_B);
             tc::mma_bf16(tmem, ah, bh, IDESC, (!first || ch > 0 || j > 0) ? 1u : 0u);
             if (MODE == 3) {
               const uint64_t al = tc::smem_desc(sA + kTileBytes + j * 2 * LBO_A, LBO_A, 128);
-              const uint64_t bl = tc::smem_desc(sB + kTileB + j * 2 * LBO_B, LBO_B, 128);
+              const uint64_t bl = tc::smem_desc_sw64(sB + kTileB + j * 32, SBO_B);
               tc::mma_bf16(tmem, ah, bl, IDESC, 1u);
               tc::mma_bf16(tmem, al, bh, IDESC, 1u);
             }
@@ -180,73 +187,43 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
       if (!ok || stall) atomicExch(&s_err, 1);
     }
     __syncwarp();
-  } else if (warp <= 4) {
-    // ------------------------------------------------------------- producers
-    const int pt = tid - 32;   // 0..127
-    bool ok = true;            // sticky; after a timeout only the barrier sequence is kept
-    int armed = 0;             // (pt == 0) stages whose A copy was issued: iterations [0, armed)
-    const int piece = pt & 7, c8 = piece >> 1, split = piece & 1;
-    for (int io = 0; io < n_off; ++io) {
-      const int b = io & 1;
-      const int ox = my_offs[3 * io + 0], oy = my_offs[3 * io + 1], oz = my_offs[3 * io + 2];
-      // source keys of this offset (buffer b was last read two offsets ago)
-      producer_bar();
-#pragma unroll
-      for (int h = 0; h < kNT / kProd; ++h) {
-        const int t = pt + h * kProd;
-        int key = 1 << (3 * level);   // no source: the all-zero node after the 8^l nodes
-        if (par0 + t < n_par) {
-          uint32_t x, y, z;
-          unmorton(8u * (par0 + t) + ctype, x, y, z);
-          // the source node, wrapped; in the isolated problem a source
-          // outside the box contributes nothing (zero-filled like padding)
-          const int ux = (int)x - ox, uy = (int)y - oy, uz = (int)z - oz;
-          const bool inbox = (unsigned)ux < (unsigned)n && (unsigned)uy < (unsigned)n && (unsigned)uz < (unsigned)n;
-          if (inbox || !iso) key = (int)morton((uint32_t)ux & (n - 1), (uint32_t)uy & (n - 1), (uint32_t)uz & (n - 1));
-        }
-        srckey[b * kNT + t] = key;
-      }
-      producer_bar();
-      const int* sk = srckey + b * kNT;
-      const uint8_t* atile = Apre + ((size_t)(off_index(ox, oy, oz) * MT + mt) * NCH) * 2 * kTileBytes;
-      for (int ch = 0; ch < NCH; ++ch) {
-        const int it = io * NCH + ch, st = it % ST;
-        if (ok && !tc::mbar_wait_bounded(&empty[st], ((uint32_t)(it / ST) & 1u) ^ 1u, kWaitNs)) ok = false;
-        if (!ok) continue;
-        const uint32_t sA = smem_base + st * STAGE_BYTES;
-        const uint32_t sB = sA + NSPLIT * kTileBytes;
-        if (pt == 0) {
-          tc::mbar_arrive_expect_tx(&afull[st], A_TX);
-          tc::bulk_g2s(sA, atile + (size_t)ch * 2 * kTileBytes, kTileBytes, &afull[st]);
-          if (MODE == 3)
-            tc::bulk_g2s(sA + kTileBytes, atile + ((size_t)ch * 2 + 1) * kTileBytes, kTileBytes, &afull[st]);
+  } else if (warp == 1) {
+    // ------------------------------------------------------- copy thread
+    if (lane == 0) {
+      bool ok = true;
+      int armed = 0;             // stages whose copies were issued: iterations [0, armed)
+      for (int io = 0; io < n_off && ok; ++io) {
+        const int ox = my_offs[3 * io + 0], oy = my_offs[3 * io + 1], oz = my_offs[3 * io + 2];
+        // sources T - o = 2 (P + d) + q: parity class q and class shift d
+        const int qx = (cx - ox) & 1, qy = (cy - oy) & 1, qz = (cz - oz) & 1;
+        const int dx = (cx - ox - qx) / 2, dy = (cy - oy - qy) / 2, dz = (cz - oz - qz) / 2;
+        const int q = qx | (qy << 1) | (qz << 2);
+        const uint8_t* atile = Apre + ((size_t)(off_index(ox, oy, oz) * MT + mt) * NCH) * 2 * kTileBytes;
+        for (int ch = 0; ch < NCH; ++ch) {
+          const int it = io * NCH + ch, st = it % ST;
+          if (!tc::mbar_wait_bounded(&empty[st], ((uint32_t)(it / ST) & 1u) ^ 1u, kWaitNs)) {
+            ok = false;
+            break;
+          }
+          const uint32_t sA = smem_base + st * STAGE_BYTES;
+          const uint32_t sB = sA + NSPLIT * kTileBytes;
+          tc::mbar_arrive_expect_tx(&full[st], TX);
+          tc::bulk_g2s(sA, atile + (size_t)ch * 2 * kTileBytes, kTileBytes, &full[st]);
+          if (MODE == 3) tc::bulk_g2s(sA + kTileBytes, atile + ((size_t)ch * 2 + 1) * kTileBytes, kTileBytes, &full[st]);
+          for (int sp = 0; sp < NSPLIT; ++sp)
+            tc::tma_load_5d(sB + sp * kTileB, &tmapB, ch * kKC, P0x + dx + kHalo, P0y + dy + kHalo, P0z + dz + kHalo,
+                            sp * 8 + q, &full[st]);
           armed = it + 1;
         }
-#pragma unroll
-        for (int pass = 0; pass < kNT / 16; ++pass) {
-          const int t = (pt >> 3) + 16 * pass;
-          if (MODE == 3 || split == 0) {
-            // full 16-byte reads only (no zero-fill operand): lanes then merge
-            // into whole-sector requests; empty slots read the zero node
-            const int key = sk[t];
-            const size_t e0 = ((size_t)key * (KP / 8) + ch * (kKC / 8) + c8) * 16 + split * 8;
-            const uint32_t d = sB + split * kTileB + (uint32_t)((c8 * (kNT / 8) + t / 8) * 128 + (t % 8) * 16);
-            tc::cp_async16_full(d, Msp + e0);
-          }
-        }
-        tc::cp_async_arrive_noinc(&full[st]);
       }
-    }
-    tc::cp_async_wait<0>();
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    // the A copies issued last may not have been consumed (after a timeout):
-    // wait (bounded) until each has landed, so no copy is in flight into this
-    // CTA's shared memory when it exits
-    if (pt == 0) {
+      // the copies issued last may not have been consumed (after a timeout):
+      // wait (bounded) until each has landed, so no copy is in flight into
+      // this CTA's shared memory when it exits
       for (int it = armed - ST > 0 ? armed - ST : 0; it < armed; ++it)
-        if (!tc::mbar_wait_bounded(&afull[it % ST], (uint32_t)(it / ST) & 1u, kWaitNs)) ok = false;
+        if (!tc::mbar_wait_bounded(&full[it % ST], (uint32_t)(it / ST) & 1u, kWaitNs)) ok = false;
+      if (!ok) atomicExch(&s_err, 1);
     }
-    if (!ok) atomicExch(&s_err, 1);
+    __syncwarp();
   } else {
     // ------------------------------------------------------------ drain warps
     const int q = warp & 3;                          // TMEM lane quadrant
@@ -271,7 +248,8 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
       tc::fence_before_sync();
       tc::mbar_arrive(&pfree);
     }
-    // final: F = total
+    // final: F = total.  Target t of the tile is the child of parent
+    // P0 + (t % 8, (t / 8) % 8, t / 64) at the CTA's child position.
     if (ok && n_off > 0 && __all_sync(0xffffffffu, atomicAdd(&s_err, 0) == 0)) {
       const int m = q * 32 + lane;
       const int gm = mt * 128 + m;
@@ -282,8 +260,10 @@ k_m2l_tc(const __nv_bfloat16* __restrict__ Msp, const uint8_t* __restrict__ Apre
         if (gm < 4 * P3) {
 #pragma unroll
           for (int k = 0; k < 32; ++k) {
-            const uint32_t t = par0 + c0 + k;
-            if (t < n_par) F[(size_t)(8u * t + ctype) * 4 * P3 + gm] = __uint_as_float(rt[k]);
+            const int t = c0 + k;
+            const uint32_t tx = 2u * (uint32_t)(P0x + t % kBX) + cx, ty = 2u * (uint32_t)(P0y + (t / kBX) % kBY) + cy,
+                           tz = 2u * (uint32_t)(P0z + t / (kBX * kBY)) + cz;
+            F[(size_t)morton(tx, ty, tz) * 4 * P3 + gm] = __uint_as_float(rt[k]);
           }
         }
       }
@@ -357,15 +337,15 @@ cudaError_t setup_one() {
 
 template <int P, int MODE>
 cudaError_t launch_one(Plan& Pl, int level, cudaStream_t s) {
-  const uint32_t n_par = 1u << (3 * (level - 1));
-  // target tiles fastest: the CTAs in flight share row tile and child type,
+  const int nh = 1 << (level - 1);
+  // target boxes fastest: the CTAs in flight share row tile and child type,
   // hence their A tiles, which L2 then serves to all of them
-  dim3 grid((n_par + kNT - 1) / kNT, TcShape<P, MODE>::MT, 8);
-  const __nv_bfloat16* Msp = static_cast<const __nv_bfloat16*>(Pl.Mbf_hi[level]);
+  dim3 grid((nh / kBX) * (nh / kBY) * (nh / kBZ), TcShape<P, MODE>::MT, 8);
+  const CUtensorMap* map = static_cast<const CUtensorMap*>(Pl.tmapB[level]);
   const uint8_t* Apre = static_cast<const uint8_t*>(Pl.Apre[level]);
   k_m2l_tc<P, MODE><<<grid, kThreads, smem_bytes<P, MODE>(), s>>>(
-      Msp, Apre, Pl.offsets[level], Pl.n_off[level], level, Pl.tc_group, Pl.F[level], Pl.d_err, Pl.wait_ns,
-      Pl.inject_stall, Pl.iso);
+      *map, Apre, Pl.offsets[level], Pl.n_off[level], level, Pl.tc_group, Pl.F[level], Pl.d_err, Pl.wait_ns,
+      Pl.inject_stall);
   return cudaGetLastError();
 }
 
@@ -388,18 +368,33 @@ cudaError_t build_a_p(Plan& Pl, int level, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Split FP32 gridlet masses into BF16 hi + lo, rows padded to KP with zeros,
-// stored [node][KP/8][hi 8 | lo 8] so one stage slice of a node is contiguous.
-__global__ void k_split_bf16(const float* __restrict__ M, int p3, int kp, size_t nodes, __nv_bfloat16* __restrict__ out) {
-  const size_t total = nodes * kp;
+// Split FP32 gridlet masses into BF16 hi + lo in the layout the tensor loads
+// read: [split][class q][z + halo][y + halo][x + halo][KP], q the node's
+// parity class ((x & 1) | (y & 1) << 1 | (z & 1) << 2) and (x, y, z) its
+// coordinates within the class (halved); the halo holds the periodic copies,
+// or zeros for the isolated problem; rows padded to KP with zeros.
+__global__ void k_split_bf16(const float* __restrict__ M, int p3, int kp, int level, int iso,
+                             __nv_bfloat16* __restrict__ out) {
+  const int nh = 1 << (level - 1), W = nh + 2 * kHalo;
+  const size_t row = (size_t)kp, cls = (size_t)W * W * W * row, total = 8 * cls;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t node = i / kp;
-    const int k = (int)(i % kp);
-    const float x = k < p3 ? M[node * p3 + k] : 0.f;
+    const int k = (int)(i % row);
+    const size_t cell = i / row;
+    const int xw = (int)(cell % W), yw = (int)((cell / W) % W), zw = (int)((cell / ((size_t)W * W)) % W);
+    const int q = (int)(cell / ((size_t)W * W * W));
+    int ux = xw - kHalo, uy = yw - kHalo, uz = zw - kHalo;
+    const bool inbox = (unsigned)ux < (unsigned)nh && (unsigned)uy < (unsigned)nh && (unsigned)uz < (unsigned)nh;
+    float x = 0.f;
+    if (k < p3 && (inbox || !iso)) {
+      ux = (ux + nh) % nh;
+      uy = (uy + nh) % nh;
+      uz = (uz + nh) % nh;
+      const uint32_t key = morton(2u * ux + (q & 1), 2u * uy + ((q >> 1) & 1), 2u * uz + (q >> 2));
+      x = M[(size_t)key * p3 + k];
+    }
     const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    const size_t o = (node * (kp / 8) + k / 8) * 16 + (k % 8);
-    out[o] = h;
-    out[o + 8] = __float2bfloat16_rn(x - __bfloat162float(h));
+    out[i] = h;
+    out[total + i] = __float2bfloat16_rn(x - __bfloat162float(h));
   }
 }
 
@@ -409,6 +404,37 @@ size_t tc_apre_bytes(int p) {
   const int p3 = p * p * p;
   const int kp = ((p3 + kKC - 1) / kKC) * kKC, nch = kp / kKC, mt = (4 * p3 + 127) / 128;
   return (size_t)kOffSlots * mt * nch * 2 * kTileBytes;
+}
+
+size_t tc_bsplit_bytes(int p, int level) {
+  const size_t W = (size_t)(1 << (level - 1)) + 2 * kHalo;
+  return 2 * 8 * W * W * W * (size_t)tc_padded_k(p) * sizeof(__nv_bfloat16);
+}
+
+// The 5-D tensor map of a level's split multipoles: dims (KP, W, W, W,
+// 16 = split x class), box (32, 8, 8, 4, 1), 64-byte swizzle.
+int make_tc_map(Plan& P, int level) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return FMM_ERR_CUDA;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  if (!P.tmapB[level]) P.tmapB[level] = new (std::nothrow) CUtensorMap;
+  if (!P.tmapB[level]) return FMM_ERR_ALLOC;
+  const cuuint64_t kp = (cuuint64_t)tc_padded_k(P.p), W = (cuuint64_t)(1 << (level - 1)) + 2 * kHalo;
+  const cuuint64_t dims[5] = {kp, W, W, W, 16};
+  const cuuint64_t strides[4] = {kp * 2, kp * 2 * W, kp * 2 * W * W, kp * 2 * W * W * W};
+  const cuuint32_t box[5] = {(cuuint32_t)kKC, (cuuint32_t)kBX, (cuuint32_t)kBY, (cuuint32_t)kBZ, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = encode(static_cast<CUtensorMap*>(P.tmapB[level]), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5,
+                            P.Mbf_hi[level], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? FMM_OK : FMM_ERR_CUDA;
 }
 
 cudaError_t launch_build_a(Plan& P, int level, cudaStream_t s) {
@@ -443,9 +469,8 @@ cudaError_t setup_m2l_tc(const Plan& P) {
 }
 
 cudaError_t launch_split_bf16(Plan& P, int level, cudaStream_t s) {
-  const size_t nodes = (size_t)1 << (3 * level);
   const int p3 = P.p * P.p * P.p;
-  k_split_bf16<<<4 * P.num_sms, 256, 0, s>>>(P.M[level], p3, tc_padded_k(P.p), nodes,
+  k_split_bf16<<<8 * P.num_sms, 256, 0, s>>>(P.M[level], p3, tc_padded_k(P.p), level, P.iso,
                                             static_cast<__nv_bfloat16*>(P.Mbf_hi[level]));
   return cudaGetLastError();
 }

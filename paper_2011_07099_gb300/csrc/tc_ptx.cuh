@@ -5,6 +5,7 @@
 // descriptions.
 #pragma once
 
+#include <cuda.h>
 #include <cstdint>
 
 namespace fmm {
@@ -49,6 +50,21 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
   d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
   d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// The same for the 64-byte-swizzled K-major layout (what a TMA tensor load
+// with CU_TENSOR_MAP_SWIZZLE_64B writes): rows of 64 bytes (32 BF16 along K),
+// 8-row groups `sbo` = 512 bytes apart; the leading offset is unused for a K
+// extent within one swizzle row (set to 16 bytes); layout type 4 at bit 61.
+// A second 16-deep K step starts 32 bytes further into the row.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
   return d;
 }
 
@@ -148,6 +164,18 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(smem_u32(mbar))
                : "memory");
+}
+
+// 5-D tiled TMA load global -> shared (async proxy) of the box at
+// coordinates (c0 innermost .. c4); completion counted in bytes on the
+// mbarrier.  c0 times the element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            int c4, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(mbar))
+      : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
