@@ -174,6 +174,22 @@ int fmm_plan_mesh_green(const fmm_plan* plan, double* out, void* stream);
 #define FMM_M2L_FFT   1
 int fmm_plan_set_m2l_algorithm(fmm_plan* plan, int algorithm);
 
+/* How the leaf stage evaluates the near zone (Sec. 2, part 3 of the
+ * potential).  FMM_NEAR_DIRECT (default): the direct sum over the 27
+ * neighbour leaves.  FMM_NEAR_FFT: the same sum by FFT convolution under
+ * non-periodic boundary conditions on a doubled grid, the approach Sec. 3
+ * takes for the near zone of a regular grid: per pair of neighbour leaves
+ * the 8^3 masses zero-padded to 16^3, the 27 x 4 kernel spectra of the near
+ * table (FP64, rounded once), FP32 transforms and products; the leaf's L2P is
+ * fused into the inverse transform.  Needs 8-cell leaves (N = 8 * 2^L);
+ * FMM_ERR_UNSUPPORTED otherwise.  Allocates the spectra (synchronous;
+ * 2^(3L) x 92 KB: 3.0 GB at 256^3, L = 5) and computes the kernel spectra,
+ * again after every re-tabulation.  FMM_NEAR_DIRECT frees them.  FMM_ERR_ARG
+ * for an unknown value, FMM_ERR_ALLOC if the spectra do not fit. */
+#define FMM_NEAR_DIRECT 0
+#define FMM_NEAR_FFT    1
+int fmm_plan_set_near_algorithm(fmm_plan* plan, int algorithm);
+
 /* Limit of every bounded device-side wait (pipeline barriers of the
  * tensor-core M2L), in milliseconds, 1..600000; default 2000.  A wait that
  * runs out makes its kernel skip the rest of its work, wait (bounded) for the

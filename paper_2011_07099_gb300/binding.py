@@ -40,6 +40,8 @@ FMM_GREEN_X = 2
 
 FMM_M2L_DENSE = 0
 FMM_M2L_FFT = 1
+FMM_NEAR_DIRECT = 0
+FMM_NEAR_FFT = 1
 
 FMM_STAGE_MULTIPOLE = 0
 FMM_STAGE_LOCAL = 1
@@ -72,6 +74,7 @@ SIGNATURES = {
     "fmm_plan_mesh_green": (_I, [_VP, _FP, _VP]),
     "fmm_plan_set_green_mesh": (_I, [_VP, _FP, _SZ]),
     "fmm_plan_set_m2l_algorithm": (_I, [_VP, _I]),
+    "fmm_plan_set_near_algorithm": (_I, [_VP, _I]),
     "fmm_plan_set_table_grid": (_I, [_VP, _FP, _SZ]),
     "fmm_table_grid_grad": (_I, [_VP, _FP, _FP, _FP, ctypes.c_float, ctypes.c_float, _FP, _FP, _VP]),
     "fmm_probe_fma_flops": (ctypes.c_double, [_I, _I]),
@@ -235,6 +238,10 @@ def fmm_plan_set_green(plan, kind, a=()):
 
 def fmm_plan_set_m2l_algorithm(plan, algorithm):
     _check(lib().fmm_plan_set_m2l_algorithm(plan, int(algorithm)), "fmm_plan_set_m2l_algorithm")
+
+
+def fmm_plan_set_near_algorithm(plan, algorithm):
+    _check(lib().fmm_plan_set_near_algorithm(plan, int(algorithm)), "fmm_plan_set_near_algorithm")
 
 
 def fmm_plan_set_green_mesh(plan, mesh):

@@ -126,6 +126,9 @@ void free_plan(Plan* P) {
     cudaFree(P->offsets[l]);
   }
   cudaFree(P->near_tab);
+  cudaFree(P->nz_K);
+  cudaFree(P->nz_M);
+  cudaFree(P->nz_P);
   cudaFree(P->d_err);
   cudaFree(P->corr_w);
   cudaFree(P->train_out);
@@ -169,6 +172,7 @@ int retabulate(Plan& P) {
       if (rc != FMM_OK) return rc;
     }
   }
+  if (P.near_fft && fmm::launch_near_fft_kernels(P, 0) != cudaSuccess) return FMM_ERR_CUDA;
   if (P.tc_ready) {
     for (int l = fmm::kTcMinLevel; l <= P.L; ++l) {
       if (!P.Apre[l]) continue;
@@ -472,6 +476,37 @@ int fmm_plan_set_m2l_algorithm(fmm_plan* plan, int algorithm) {
     }
   }
   return set_err(FMM_OK);
+}
+
+int fmm_plan_set_near_algorithm(fmm_plan* plan, int algorithm) {
+  if (!plan || (algorithm != FMM_NEAR_DIRECT && algorithm != FMM_NEAR_FFT)) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  if (algorithm == FMM_NEAR_DIRECT) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return set_err(FMM_ERR_CUDA);
+    cudaFree(P.nz_K);
+    cudaFree(P.nz_M);
+    cudaFree(P.nz_P);
+    P.nz_K = P.nz_M = P.nz_P = nullptr;
+    P.near_fft = 0;
+    return set_err(FMM_OK);
+  }
+  if (!fmm::near_fft_supported(P)) return set_err(FMM_ERR_UNSUPPORTED);
+  if (!P.nz_K) {
+    size_t nK, nM, nP;
+    fmm::near_fft_counts(P, nK, nM, nP);
+    if (!dev_alloc(&P.nz_K, nK) || !dev_alloc(&P.nz_M, nM) || !dev_alloc(&P.nz_P, nP)) {
+      cudaFree(P.nz_K);
+      cudaFree(P.nz_M);
+      cudaFree(P.nz_P);
+      P.nz_K = P.nz_M = P.nz_P = nullptr;
+      return set_err(FMM_ERR_ALLOC);
+    }
+    // the all-zero spectrum of out-of-box neighbours sits after each chunk's leaves
+    FMM_CUDA_TRY(cudaMemset(P.nz_M, 0, sizeof(float2) * nM));
+  }
+  P.near_fft = 1;
+  FMM_CUDA_TRY(fmm::launch_near_fft_kernels(P, 0));
+  return set_err(cudaDeviceSynchronize() == cudaSuccess ? FMM_OK : FMM_ERR_CUDA);
 }
 
 int fmm_plan_set_timeout_ms(fmm_plan* plan, int ms) {

@@ -105,6 +105,12 @@ struct Plan {
   int m2l_fft = 0;                         // FFT form of the interaction zone at the fine levels (ablation)
   void* fft = nullptr;                     // its cuFFT plans and buffers (m2l_fft.cu)
   int tc_min_level = kTcMinLevel;          // first level on the tensor cores in the mixed forms
+  // near zone by FFT (p2p_fft.cu; 8-cell leaves): kernel spectra [72][27][4][32],
+  // source spectra [72][leaves + 1][32] (last: all zero), target spectra [leaves][4][2304]
+  int near_fft = 0;
+  float2* nz_K = nullptr;
+  float2* nz_M = nullptr;
+  float2* nz_P = nullptr;
   // learned table correction (MLP weights) and its training buffers
   float* corr_w = nullptr;                 // mlp::kParams weights (device) or unset
   int has_corr = 0;
@@ -181,6 +187,14 @@ cudaError_t launch_m2l_fft(Plan& P, int level, cudaStream_t s);
 void free_fft(Plan& P);
 cudaError_t launch_l2l(Plan& P, int level, cudaStream_t s);       // F[level] -> F[level+1] (adds)
 cudaError_t launch_p2p(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s);
+// The near zone by FFT (p2p_fft.cu): whether the plan's shape allows it, the
+// float2 counts of its kernel, source and target spectra, function attributes, the plan-time kernel spectra (after every
+// re-tabulation) and the leaf stage itself (launch_p2p dispatches to it).
+bool near_fft_supported(const Plan& P);
+void near_fft_counts(const Plan& P, size_t& nK, size_t& nM, size_t& nP);
+cudaError_t setup_near_fft(const Plan& P);
+cudaError_t launch_near_fft_kernels(Plan& P, cudaStream_t s);
+cudaError_t launch_near_fft(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s);
 cudaError_t setup_m2l_tc(const Plan& P);
 cudaError_t setup_learn();
 cudaError_t launch_residual(const float* phi, const float* acc, const float* tphi, const float* tacc, size_t n3,

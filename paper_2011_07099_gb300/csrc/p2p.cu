@@ -485,13 +485,17 @@ cudaError_t setup_p2p(const Plan& P) {
     case 3: return setup_s<3>();
     case 4: return setup_s<4>();
     case 6: return setup_s<6>();
-    case 8: return setup_s<8>();
+    case 8: {
+      const cudaError_t e = setup_s<8>();
+      return e != cudaSuccess ? e : setup_near_fft(P);
+    }
     case 16: return cudaFuncSetAttribute(k_p2p16, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_p2p(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s) {
+  if (P.near_fft) return launch_near_fft(P, rho, phi, acc, s);
   switch (P.S) {
     case 1: return launch_s<1>(P, rho, phi, acc, s);
     case 2: return launch_s<2>(P, rho, phi, acc, s);

@@ -1,0 +1,386 @@
+// Leaf stage by fast Fourier transforms: the near zone (P2P) as a sum of
+// zero-padded convolutions, the leaf's L2P fused into the inverse transform.
+//
+// Sec. 3 computes the near zone of a regular grid with an FFT under
+// non-periodic boundary conditions, obtained by doubling the grid.  Here that
+// is done per pair of leaves.  For a target leaf T of S = 8 cells per side and
+// one of its 27 neighbour leaves T + o (o in {-1, 0, 1}^3), the near-zone
+// field at cell r of T is the linear convolution
+//   Phi_T(r) += sum_{r'} K(r - r' - S o) m_{T+o}(r'),   r, r' in [0, S)^3,
+// whose lags r - r' lie in [-(S-1), S-1]^3.  Padded to M = 2S points per axis
+// that linear convolution is a circular one with no lag wrapped onto another,
+// so on the M^3 spectrum
+//   Phi^_T(k) = sum_o K^_o(k) m^_{T+o}(k),
+// K^_o the transform of u -> K(u - S o) placed at u mod M (u in [-(S-1), S-1]^3,
+// the lag S never occurs and holds 0).  K = (G, -dG/dx, -dG/dy, -dG/dz) at the
+// cell offsets: the plan's near table (the same FP32 values the direct sum
+// uses), so the result is the direct sum's up to rounding.
+//
+// Kernels (all spectra are real-input half spectra, kx in [0, M/2]):
+//   k_nz_kernel  plan time: the 27 x 4 kernel spectra, in FP64, rounded once
+//   k_nz_fwd     per leaf: the spectrum of its zero-padded masses
+//   k_nz_mac     per (tile of 4^3 target leaves, chunk of 32 frequencies): the
+//                27-term sums for 4 fields, written per target leaf
+//   k_nz_inv     per target leaf: 4 inverse transforms, only the S^3 cells kept,
+//                plus the L2P far field; writes the final potential and
+//                acceleration.
+// Transforms are direct DFTs along each axis (8 nonzero inputs forward, 8
+// kept outputs inverse), with twiddles from sincospi in FP64.
+#include "fmm_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace fmm {
+namespace {
+
+constexpr int kNS = 8;                       // leaf cells per side
+constexpr int kNM = 2 * kNS;                 // padded transform size
+constexpr int kNX = kNM / 2 + 1;             // half-spectrum extent along x
+constexpr int kNK = kNM * kNM * kNX;         // frequencies per spectrum (2304)
+constexpr int kNC = 32;                      // frequencies per chunk
+constexpr int kNCH = kNK / kNC;              // chunks (72)
+constexpr int kNO = 27;                      // neighbour offsets
+constexpr int kNT = 4;                       // target leaves per tile side
+constexpr int kNH = kNT + 2;                 // source leaves per halo side
+constexpr int kThr = 256;
+static_assert(kNK % kNC == 0, "chunking");
+
+// linear frequency index: k = (kz * M + ky) * (M/2 + 1) + kx
+
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+// e^{-2 pi i j / M}, j = 0 .. M-1, into shared memory (FP64 -> FP32)
+__device__ __forceinline__ void twiddles(float2* w, int tid) {
+  if (tid < kNM) {
+    double s, c;
+    sincospi((double)tid / (kNM / 2), &s, &c);
+    w[tid] = make_float2((float)c, (float)-s);
+  }
+}
+
+// The kernel's value for field f at lag d (cells), from the folded near table
+// (|d_i| in [0, 2S-1]); the gradient fields take the sign of their own
+// component as the direct sum does.
+__device__ __forceinline__ double near_value(const float4* __restrict__ tab, int f, int dx, int dy, int dz) {
+  constexpr int TD = 2 * kNS;
+  const int ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy, az = dz < 0 ? -dz : dz;
+  const float4 t = __ldg(tab + (az * TD + ay) * TD + ax);
+  switch (f) {
+    case 0: return (double)t.x;
+    case 1: return dx >= 0 ? (double)t.y : -(double)t.y;
+    case 2: return dy > 0 ? (double)t.z : (dy < 0 ? -(double)t.z : 0.0);
+    default: return dz > 0 ? (double)t.w : (dz < 0 ? -(double)t.w : 0.0);
+  }
+}
+
+// Kernel spectra: CTA (o, f) transforms u -> K_f(u - S o) on the M^3 grid in
+// FP64 (three separable passes), writing K^[chunk][o][f][32] as FP32.
+__global__ void __launch_bounds__(kThr) k_nz_kernel(const float4* __restrict__ near_tab, float2* __restrict__ Khat) {
+  __shared__ double2 w64[kNM];
+  extern __shared__ double2 sd[];
+  double2* T1 = sd;                 // [vz][vy][kx]
+  double2* T2 = sd + kNM * kNM * kNX;   // [vz][ky][kx]
+  const int o = blockIdx.x / 4, f = blockIdx.x % 4, tid = threadIdx.x;
+  const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+  if (tid < kNM) {
+    double s, c;
+    sincospi((double)tid / (kNM / 2), &s, &c);
+    w64[tid] = make_double2(c, -s);
+  }
+  __syncthreads();
+  auto lag = [](int v) { return v < kNS ? v : v - kNM; };   // v = M/2 = S is never a lag
+  for (int i = tid; i < kNM * kNM * kNX; i += blockDim.x) {
+    const int kx = i % kNX, vy = (i / kNX) % kNM, vz = i / (kNX * kNM);
+    double re = 0.0, im = 0.0;
+    if (vy != kNS && vz != kNS) {
+      for (int vx = 0; vx < kNM; ++vx) {
+        if (vx == kNS) continue;
+        const double a = near_value(near_tab, f, lag(vx) - kNS * ox, lag(vy) - kNS * oy, lag(vz) - kNS * oz);
+        const double2 t = w64[(kx * vx) % kNM];
+        re += a * t.x;
+        im += a * t.y;
+      }
+    }
+    T1[i] = make_double2(re, im);
+  }
+  __syncthreads();
+  for (int i = tid; i < kNM * kNM * kNX; i += blockDim.x) {
+    const int kx = i % kNX, ky = (i / kNX) % kNM, vz = i / (kNX * kNM);
+    double re = 0.0, im = 0.0;
+    for (int vy = 0; vy < kNM; ++vy) {
+      const double2 a = T1[(vz * kNM + vy) * kNX + kx], t = w64[(ky * vy) % kNM];
+      re += a.x * t.x - a.y * t.y;
+      im += a.x * t.y + a.y * t.x;
+    }
+    T2[i] = make_double2(re, im);
+  }
+  __syncthreads();
+  for (int k = tid; k < kNK; k += blockDim.x) {
+    const int kx = k % kNX, ky = (k / kNX) % kNM, kz = k / (kNX * kNM);
+    double re = 0.0, im = 0.0;
+    for (int vz = 0; vz < kNM; ++vz) {
+      const double2 a = T2[(vz * kNM + ky) * kNX + kx], t = w64[(kz * vz) % kNM];
+      re += a.x * t.x - a.y * t.y;
+      im += a.x * t.y + a.y * t.x;
+    }
+    Khat[(((size_t)(k / kNC) * kNO + o) * 4 + f) * kNC + k % kNC] = make_float2((float)re, (float)im);
+  }
+}
+
+// Source spectra: CTA per leaf; masses m = (rho - mean) / N^3 (mean as hi + lo,
+// as in the direct kernel) zero-padded to M^3.  Writes m^[chunk][leaf][32];
+// the slot after the last leaf is the all-zero spectrum of an out-of-box
+// neighbour (isolated problem), cleared at allocation.
+__global__ void __launch_bounds__(kThr) k_nz_fwd(const float* __restrict__ rho, const double* __restrict__ mean, int N,
+                                                int L, float2* __restrict__ Mhat) {
+  __shared__ float2 w[kNM];
+  __shared__ float m[kNS * kNS * kNS];
+  __shared__ float2 A[kNS * kNS * kNX];    // [z][y][kx]
+  __shared__ float2 B[kNS * kNM * kNX];    // [z][ky][kx]
+  const int tid = threadIdx.x;
+  const unsigned leaf = blockIdx.x, nl3 = 1u << (3 * L);
+  twiddles(w, tid);
+  uint32_t lx, ly, lz;
+  unmorton(leaf, lx, ly, lz);
+  const double mu = *mean;
+  const float mu_hi = (float)mu, mu_lo = (float)(mu - (double)mu_hi);
+  const float inv_vol = (float)(1.0 / ((double)N * N * N));
+  for (int i = tid; i < kNS * kNS * kNS; i += blockDim.x) {
+    const int x = i % kNS, y = (i / kNS) % kNS, z = i / (kNS * kNS);
+    const float r = __ldg(rho + ((size_t)(lz * kNS + z) * N + (ly * kNS + y)) * N + lx * kNS + x);
+    m[i] = ((r - mu_hi) - mu_lo) * inv_vol;
+  }
+  __syncthreads();
+  for (int i = tid; i < kNS * kNS * kNX; i += blockDim.x) {     // x: 8 real inputs -> kx in [0, M/2]
+    const int kx = i % kNX, zy = i / kNX;
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int x = 0; x < kNS; ++x) {
+      const float v = m[zy * kNS + x];
+      const float2 t = w[(kx * x) % kNM];
+      acc.x = fmaf(v, t.x, acc.x);
+      acc.y = fmaf(v, t.y, acc.y);
+    }
+    A[i] = acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < kNS * kNM * kNX; i += blockDim.x) {     // y: 8 nonzero inputs -> 16
+    const int kx = i % kNX, ky = (i / kNX) % kNM, z = i / (kNX * kNM);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int y = 0; y < kNS; ++y) cfma(acc, A[(z * kNS + y) * kNX + kx], w[(ky * y) % kNM]);
+    B[i] = acc;
+  }
+  __syncthreads();
+  for (int k = tid; k < kNK; k += blockDim.x) {                 // z: 8 nonzero inputs -> 16
+    const int kxy = k % (kNX * kNM), kz = k / (kNX * kNM);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int z = 0; z < kNS; ++z) cfma(acc, B[z * kNM * kNX + kxy], w[(kz * z) % kNM]);
+    Mhat[((size_t)(k / kNC) * (nl3 + 1) + leaf) * kNC + k % kNC] = acc;
+  }
+}
+
+// Spectral sums: CTA (tile of 4^3 target leaves, chunk c).  Thread (g, f):
+// frequency c*32 + f of the 8 target leaves of group g (a 4 x 2 x 1 slab),
+// 4 fields each.
+__global__ void __launch_bounds__(kThr, 2) k_nz_mac(const float2* __restrict__ Khat, const float2* __restrict__ Mhat,
+                                                   float2* __restrict__ Phat, int L, int iso) {
+  extern __shared__ float4 sm4[];
+  float2* sK = reinterpret_cast<float2*>(sm4);          // [o][f][32]
+  float2* sM = sK + kNO * 4 * kNC;                      // [halo leaf][32]
+  const int tid = threadIdx.x;
+  const int nl = 1 << L, nt = nl / kNT;
+  const unsigned nl3 = 1u << (3 * L);
+  const int t = blockIdx.x, c = blockIdx.y;
+  const int TX = t % nt, TY = (t / nt) % nt, TZ = t / (nt * nt);
+  {
+    const float2* src = Khat + (size_t)c * kNO * 4 * kNC;
+    for (int i = tid; i < kNO * 4 * kNC / 2; i += blockDim.x)
+      tc::cp_async16(tc::smem_u32(sK + 2 * i), src + 2 * i, 16u);
+    for (int i = tid; i < kNH * kNH * kNH * (kNC / 2); i += blockDim.x) {
+      const int h = i / (kNC / 2), q = i % (kNC / 2);
+      const int hx = h % kNH, hy = (h / kNH) % kNH, hz = h / (kNH * kNH);
+      int gx = TX * kNT + hx - 1, gy = TY * kNT + hy - 1, gz = TZ * kNT + hz - 1;
+      unsigned leaf;
+      if (iso && (gx < 0 || gy < 0 || gz < 0 || gx >= nl || gy >= nl || gz >= nl)) {
+        leaf = nl3;                                     // the all-zero spectrum
+      } else {
+        gx = (gx + nl) % nl;
+        gy = (gy + nl) % nl;
+        gz = (gz + nl) % nl;
+        leaf = morton((uint32_t)gx, (uint32_t)gy, (uint32_t)gz);
+      }
+      tc::cp_async16(tc::smem_u32(sM + h * kNC + 2 * q), Mhat + ((size_t)c * (nl3 + 1) + leaf) * kNC + 2 * q, 16u);
+    }
+    tc::cp_async_commit();
+    tc::cp_async_wait<0>();
+    __syncthreads();
+  }
+  const int f = tid % kNC, g = tid / kNC;
+  const int hbase = 2 * (g & 1) * kNH + (g >> 1) * kNH * kNH;   // halo index of the group's first leaf, less (1,1,1)
+  float2 acc[8][4];
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[j][q] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int o = 0; o < kNO; ++o) {
+    const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+    float2 k[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) k[q] = sK[(o * 4 + q) * kNC + f];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int h = hbase + ((j & 3) + ox + 1) + kNH * ((j >> 2) + oy + 1) + kNH * kNH * (oz + 1);
+      const float2 mv = sM[h * kNC + f];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cfma(acc[j][q], k[q], mv);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint32_t lx = TX * kNT + (j & 3), ly = TY * kNT + 2 * (g & 1) + (j >> 2), lz = TZ * kNT + (g >> 1);
+    const size_t leaf = morton(lx, ly, lz);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Phat[(leaf * 4 + q) * kNK + (size_t)c * kNC + f] = acc[j][q];
+  }
+}
+
+// Shared-memory carve-up of the inverse kernel (floats), for order p.
+struct NzInvSmem {
+  int w8, far, in, t1, t2, spec, zb, yb, total;
+  __host__ __device__ NzInvSmem(int p) {
+    const int p3 = p * p * p;
+    w8 = 0;                                           // p S float2
+    far = (2 * p * kNS + 3) / 4 * 4;                  // 4 S^3 floats
+    in = far + 4 * kNS * kNS * kNS;                   // 4 p^3 floats
+    t1 = in + 4 * p3;                                 // 4 p p S floats
+    t2 = t1 + 4 * p * p * kNS;                        // 4 p S S floats
+    spec = (t2 + 4 * p * kNS * kNS + 3) / 4 * 4;      // M^2 (M/2+1) float2
+    zb = spec + 2 * kNK;                              // S M (M/2+1) float2
+    yb = zb + 2 * kNS * kNM * kNX;                    // S S (M/2+1) float2
+    total = yb + 2 * kNS * kNS * kNX;
+  }
+};
+
+// Inverse transforms of one target leaf's 4 field spectra (only the S^3
+// cells of the leaf are formed), plus the L2P far field; writes the results.
+__global__ void __launch_bounds__(kThr) k_nz_inv(const float2* __restrict__ Phat, int N, int L, int p,
+                                                const float* __restrict__ Fleaf, const float2* __restrict__ wp2m,
+                                                float* __restrict__ phi, float* __restrict__ acc_out) {
+  __shared__ float2 w[kNM];
+  extern __shared__ float4 sm4[];
+  float* base = reinterpret_cast<float*>(sm4);
+  const NzInvSmem lay(p);
+  float2* W8 = reinterpret_cast<float2*>(base + lay.w8);
+  float* far = base + lay.far;
+  float* in = base + lay.in;
+  float2* spec = reinterpret_cast<float2*>(base + lay.spec);
+  float2* Z = reinterpret_cast<float2*>(base + lay.zb);
+  float2* Y = reinterpret_cast<float2*>(base + lay.yb);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const unsigned leaf = blockIdx.x;
+  const int p3 = p * p * p;
+  const size_t N3 = (size_t)N * N * N;
+  twiddles(w, tid);
+  for (int i = tid; i < p * kNS; i += nthr) W8[i] = wp2m[i];
+  const float* src = Fleaf + (size_t)leaf * 4 * p3;
+  for (int i = tid; i < 4 * p3; i += nthr) in[i] = __ldg(src + i);
+  __syncthreads();
+  // L2P: far[f][cz][cy][cx] = sum_s l_s(cz) l_s(cy) l_s(cx) F[f][s] (ends with a barrier)
+  contract3(in, base + lay.t1, base + lay.t2, far, 4, p, kNS, W8, kNS, true, tid, nthr);
+  uint32_t lx, ly, lz;
+  unmorton(leaf, lx, ly, lz);
+  const float scale = 1.f / (float)(kNM * kNM * kNM);
+  for (int q = 0; q < 4; ++q) {
+    const float4* s4 = reinterpret_cast<const float4*>(Phat + ((size_t)leaf * 4 + q) * kNK);
+    float4* d4 = reinterpret_cast<float4*>(spec);
+    for (int i = tid; i < kNK / 2; i += nthr) d4[i] = __ldg(s4 + i);
+    __syncthreads();
+    for (int i = tid; i < kNS * kNM * kNX; i += nthr) {      // z: 16 -> the 8 kept planes
+      const int kxy = i % (kNX * kNM), z = i / (kNX * kNM);
+      float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int kz = 0; kz < kNM; ++kz) {
+        const float2 t = w[(kz * z) % kNM];
+        cfma(a, spec[kz * kNM * kNX + kxy], make_float2(t.x, -t.y));
+      }
+      Z[i] = a;
+    }
+    __syncthreads();
+    for (int i = tid; i < kNS * kNS * kNX; i += nthr) {      // y: 16 -> the 8 kept rows
+      const int kx = i % kNX, y = (i / kNX) % kNS, z = i / (kNX * kNS);
+      float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int ky = 0; ky < kNM; ++ky) {
+        const float2 t = w[(ky * y) % kNM];
+        cfma(a, Z[(z * kNM + ky) * kNX + kx], make_float2(t.x, -t.y));
+      }
+      Y[i] = a;
+    }
+    __syncthreads();
+    for (int i = tid; i < kNS * kNS * kNS; i += nthr) {      // x: half spectrum -> 8 real cells
+      const int x = i % kNS, zy = i / kNS;
+      const float2* yr = Y + zy * kNX;
+      float v = 0.f;
+#pragma unroll
+      for (int kx = 1; kx < kNX - 1; ++kx) {
+        const float2 t = w[(kx * x) % kNM];            // Re(Y e^{+i theta}) = Y.x cos + Y.y (-sin)
+        v = fmaf(yr[kx].x, t.x, v);
+        v = fmaf(yr[kx].y, t.y, v);
+      }
+      v = 2.f * v + yr[0].x + ((x & 1) ? -yr[kNX - 1].x : yr[kNX - 1].x);
+      const int y = zy % kNS, z = zy / kNS;
+      const size_t o = ((size_t)(lz * kNS + z) * N + (ly * kNS + y)) * N + lx * kNS + x;
+      const float r = v * scale + far[q * kNS * kNS * kNS + i];
+      if (q == 0) phi[o] = r;
+      else acc_out[(size_t)(q - 1) * N3 + o] = r;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+bool near_fft_supported(const Plan& P) { return P.S == kNS && P.L >= 2; }
+
+void near_fft_counts(const Plan& P, size_t& nK, size_t& nM, size_t& nP) {
+  const size_t nl3 = (size_t)1 << (3 * P.L);
+  nK = (size_t)kNCH * kNO * 4 * kNC;
+  nM = (size_t)kNCH * (nl3 + 1) * kNC;
+  nP = nl3 * 4 * kNK;
+}
+
+cudaError_t setup_near_fft(const Plan& P) {
+  cudaError_t e = cudaFuncSetAttribute(k_nz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(2 * sizeof(double2) * kNM * kNM * kNX));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_nz_mac, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(float2) * (kNO * 4 * kNC + kNH * kNH * kNH * kNC)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_nz_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(sizeof(float) * NzInvSmem(kMaxOrder).total));
+}
+
+cudaError_t launch_near_fft_kernels(Plan& P, cudaStream_t s) {
+  k_nz_kernel<<<kNO * 4, kThr, 2 * sizeof(double2) * kNM * kNM * kNX, s>>>(P.near_tab, P.nz_K);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_near_fft(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s) {
+  const unsigned nl3 = 1u << (3 * P.L);
+  const int nt = (1 << P.L) / kNT;
+  k_nz_fwd<<<nl3, kThr, 0, s>>>(rho, P.d_mean, P.N, P.L, P.nz_M);
+  k_nz_mac<<<dim3(nt * nt * nt, kNCH), kThr, sizeof(float2) * (kNO * 4 * kNC + kNH * kNH * kNH * kNC), s>>>(
+      P.nz_K, P.nz_M, P.nz_P, P.L, P.iso);
+  k_nz_inv<<<nl3, kThr, sizeof(float) * NzInvSmem(P.p).total, s>>>(P.nz_P, P.N, P.L, P.p, P.F[P.L], P.w_p2m, phi,
+                                                                  acc);
+  return cudaGetLastError();
+}
+
+}  // namespace fmm
