@@ -141,8 +141,17 @@ def workload_density(n, field):
 # DRAM bytes (read + write) of one k_p2p launch, from an ncu capture of the
 # current kernel at 256^3, p = 6, L = 5 (dram__bytes_read.sum +
 # dram__bytes_write.sum); not measured in this run
-P2P_TRAFFIC = {(256, 5, 6): 419.8e6}
-P2P_TRAFFIC_SOURCE = "ncu capture of the current k_p2p at 256^3 p=6 (dram__bytes read+write), not measured in this run"
+P2P_TRAFFIC = {(256, 5, 6): 419.3e6}
+# DRAM bytes (read + write) of one launch of the tensor-core M2L at the leaf
+# level and of the three near-zone FFT kernels together, from ncu captures
+# of the current kernels at 256^3 p=6 (profiles/); None where not captured
+M2L_TC_TRAFFIC = {(256, 5, 6): 1603.3e6}
+M2L_TC_TRAFFIC_SOURCE = ("ncu capture of the current k_m2l_tc at 256^3 p=6, level 5 (dram__bytes read 1503.1 MB + "
+                         "write 100.2 MB), not measured in this run")
+NEAR_FFT_TRAFFIC = {}
+NEAR_FFT_TRAFFIC_SOURCE = "ncu capture of the current k_nz_fwd + k_nz_mac + k_nz_inv at 256^3 p=6"
+P2P_TRAFFIC_SOURCE = ("ncu capture of the current k_p2p at 256^3 p=6 (dram__bytes read 197.6 MB + write 221.7 MB), "
+                      "not measured in this run")
 
 
 def measure_fp32_peak(B, dev, stream, reps=40):
@@ -189,6 +198,19 @@ def m2l_flops(L, p):
         n_off = 37 if lev == 2 else 189
         tot += 2.0 * 4 * p ** 3 * p ** 3 * n_off * 8 ** lev
     return tot
+
+
+def near_fft_flops(N, L, p):
+    """Arithmetic of the near zone by FFT per solve, counted as the kernels do
+    it (direct DFTs per axis, 8-cell leaves, 16^3 padded transforms): the
+    spectral sums (27 offsets x 4 fields x 2304 frequencies, 8 flop per complex
+    multiply-add), the forward transform of the masses and the four inverse
+    transforms that keep only the leaf's cells."""
+    leaves = 8 ** L
+    mac = 27 * 4 * 2304 * 8
+    fwd = 2 * (64 * 9 * 8 * 2 + 8 * 16 * 9 * 8 * 4 + 16 * 16 * 9 * 8 * 4)        # FMA x 2 per axis pass
+    inv = 4 * 2 * (8 * 16 * 9 * 16 * 4 + 8 * 8 * 9 * 16 * 4 + 512 * 8 * 2)   # per field, 4 fields
+    return float(leaves * (mac + fwd + inv))
 
 
 def cpu_baseline():
@@ -246,13 +268,20 @@ def learned_correction(args):
             "applied_to": "M2L tables, levels 2..L"}
 
 
+def near_fft_used(args):
+    """The near zone by FFT (Sec. 3's doubled-grid convolution) needs 8-cell leaves."""
+    return args.near == "fft" and (args.n >> args.L) == 8
+
+
 def headline_config(args, learned, ws):
     """The `config` object of the headline workload; both arms print it."""
     n, L, p = args.n, args.L, args.p
+    near = "near zone by FFT on the doubled grid" if near_fft_used(args) else "near zone by direct sum"
     return {"workload": f"{n}^3 lognormal sigma=0.5 (seeded), order p={p}, L={L} (S={n >> L}), "
-                        f"M2L levels>=4 {args.precision}, levels 2-3 extended-precision CUDA-core"
+                        f"M2L levels>=4 {args.precision}, levels 2-3 extended-precision CUDA-core, {near}"
                         + (", learned table correction" if learned else ""),
-            "N": n, "L": L, "order": p, "precision": args.precision,
+            "N": n, "L": L, "order": p, "precision": args.precision, "near_zone": args.near if near_fft_used(args)
+            else "direct",
             "learned_correction": None if learned is None else {k: v for k, v in learned.items() if k != "path"},
             "l2_flush": "256 MB buffer written between timed steps",
             "parallelism": f"replicas x{ws}"}
@@ -331,26 +360,34 @@ def device_check(B, plan):
     return "ok" if rc == B.FMM_OK else B.lib().fmm_error_string(rc).decode()
 
 
-def launches_per_solve(L, tc, p=6):
-    # mean (2) + P2M + M2M per level + M2L per level + L2L per level + P2P;
+def launches_per_solve(L, tc, p=6, near_fft=False):
+    # mean (2) + P2M + M2M per level + M2L per level + L2L per level + P2P
+    # (three kernels with the near zone by FFT: forward, sums, inverse + L2P);
     # M2L of the coarse levels (2-3, and every level above the leaves at
     # order >= 7) adds the FP64 range-sum kernel, tensor-core levels the
     # BF16 split kernel
     wide = lambda lev: lev <= 3 or (p >= 7 and lev < L)
     tc_first = max(4, L) if p >= 7 else 4
     m2l = sum(2 if (wide(lev) or (tc and lev >= tc_first)) else 1 for lev in range(2, L + 1))
-    return 2 + 1 + (L - 2) + m2l + (L - 2) + 1
+    return 2 + 1 + (L - 2) + m2l + (L - 2) + (3 if near_fft else 1)
 
 
-def solve_roofline(n, L, p, tc, ms, peaks, fp32_tflops):
+def solve_roofline(n, L, p, tc, ms, peaks, fp32_tflops, near_fft=False):
     """Ideal time of the whole solve (each step at its own bound: FP32 FMA,
-    BF16 tensor (executed products), HBM bytes) against the measured step."""
+    BF16 tensor (executed products), HBM bytes) against the measured step.
+    With the near zone by FFT its term is the larger of its arithmetic at the
+    FP32 peak and its spectra's HBM round trips (source spectra written and
+    read, target spectra written and read: 2 x (18 + 74) KB per leaf)."""
     fp32 = fp32_tflops * 1e12
     bf16 = peaks.get("bf16_tflops_sustained", 1700.0) * 1e12
     hbm = peaks.get("hbm_gbs", 6500.0) * 1e9
     p3 = p ** 3
     tc_first = max(4, L) if p >= 7 else 4
-    t = {"p2p": p2p_flops(n, L) / fp32, "m2l_cuda_cores": 0.0, "m2l_tensor": 0.0}
+    if near_fft:
+        near = max(near_fft_flops(n, L, p) / fp32, (8 ** L) * 2 * (18432 + 73728) / peaks.get("hbm_gbs", 6500.0) / 1e9)
+        t = {"near_fft": near, "m2l_cuda_cores": 0.0, "m2l_tensor": 0.0}
+    else:
+        t = {"p2p": p2p_flops(n, L) / fp32, "m2l_cuda_cores": 0.0, "m2l_tensor": 0.0}
     for lev in range(2, L + 1):
         f = 2.0 * 4 * p3 * p3 * (37 if lev == 2 else 189) * 8 ** lev
         if tc and lev >= tc_first:
@@ -406,6 +443,9 @@ def run_ours(args):
     if learned is not None:
         w = torch.from_numpy(np.load(learned["path"])["w"].astype(np.float32)).to(dev)
         B.fmm_plan_set_correction(plan.handle, w)   # tabulated once at plan time; BF16 inference
+    near_fft = near_fft_used(args)
+    if near_fft:
+        B.fmm_plan_set_near_algorithm(plan.handle, B.FMM_NEAR_FFT)
     with ClockSampler(dev.index) as clk:
         step_ms, stage, wall = _time_solves(B, plan, rho, phi, acc, args.steps, args.warmup, l2_flush, stream,
                                             barrier)
@@ -437,6 +477,8 @@ def run_ours(args):
         nplan = B.Plan(n, L, p)
         if tc:
             nplan.set_precision(prec)
+        if near_fft:
+            B.fmm_plan_set_near_algorithm(nplan.handle, B.FMM_NEAR_FFT)
         nphi = torch.empty_like(phi)
         nacc = torch.empty_like(acc)
         nplan.solve(rho, nphi, nacc)
@@ -458,42 +500,77 @@ def run_ours(args):
     for lev in range(2, L + 1):
         stage_ms[f"m2l_level{lev}"] = st[B.FMM_TIME_M2L_LEVEL0 + lev]
 
-    # the plain FP32 form on the same field, same run (the comparison the metric names)
+    # the plain FP32 form on the same field, same run (the comparison the metric
+    # names: FP32 M2L, near zone by direct sum), and the two forms between it
+    # and the headline (one change each), so the speed-up can be split up
+    def time_form(form_prec, form_fft, form_learned):
+        fplan = B.Plan(n, L, p)
+        if form_prec != B.FMM_PREC_FP32:
+            fplan.set_precision(form_prec)
+        if form_learned is not None:
+            B.fmm_plan_set_correction(fplan.handle, w)
+        if form_fft:
+            B.fmm_plan_set_near_algorithm(fplan.handle, B.FMM_NEAR_FFT)
+        fms, fstage, _ = _time_solves(B, fplan, rho, phi, acc, max(1, min(args.steps, 3)),
+                                      max(1, min(args.warmup, 2)), l2_flush, stream, barrier)
+        fm = slowest_rank_ms(statistics.mean(fms), ws, dev)
+        res = {"value": whole_job_cells_per_s(ws, n, fm), "ms_per_step": fm,
+               "m2l_ms": statistics.mean(s_[B.FMM_TIME_M2L] for s_ in fstage),
+               "p2p_ms": statistics.mean(s_[B.FMM_TIME_P2P] for s_ in fstage),
+               "device_check": device_check(B, fplan)}
+        fplan.close()
+        return res
+
     plain = None
+    forms = {}
     if tc and not args.no_plain:
-        pplan = B.Plan(n, L, p)
-        pms, pstage, _ = _time_solves(B, pplan, rho, phi, acc, max(1, min(args.steps, 3)), max(1, min(args.warmup, 2)),
-                                      l2_flush, stream, barrier)
-        checks["plain_fp32"] = device_check(B, pplan)
-        pm_ = slowest_rank_ms(statistics.mean(pms), ws, dev)
-        plain = {"value": whole_job_cells_per_s(ws, n, pm_), "ms_per_step": pm_,
-                 "m2l_ms": statistics.mean(s[B.FMM_TIME_M2L] for s in pstage),
-                 "p2p_ms": statistics.mean(s[B.FMM_TIME_P2P] for s in pstage)}
-        pplan.close()
+        plain = time_form(B.FMM_PREC_FP32, False, None)
+        checks["plain_fp32"] = plain.pop("device_check")
+        if near_fft:
+            forms["plain_fp32_near_fft"] = time_form(B.FMM_PREC_FP32, True, None)
+            forms["mixed_near_direct"] = time_form(prec, False, learned)
+        # phi/acc now hold the last form's result: the timed result was
+        # copied to the host (host leg) and measured (error statement) above
 
     peaks, src = _peaks()
     fma = measure_fp32_peak(B, dev, stream)
     fp32_peak = fma["tflops"]
     dominant = max(names, key=lambda k: stage_ms[k])
-    p2p_ach = p2p_flops(n, L) / (stage_ms["p2p_l2p"] / 1000.0) / 1e12
-    traffic = P2P_TRAFFIC.get((n, L, p))
-    roof_p2p = {"kernel": "k_p2p (fused L2P + near-zone sum)", "bound": "alu", "achieved": p2p_ach,
-                "peak": fp32_peak, "unit": "TFLOP/s", "frac": p2p_ach / fp32_peak,
-                "traffic": traffic, "traffic_source": P2P_TRAFFIC_SOURCE if traffic else None,
-                "peak_source": "measured (of measured): " + fma["how"], "fp32_probe": fma}
-    tc_levels = [lev for lev in range(4, L + 1)] if tc else []
+    roof_p2p = roof_near = None
+    if near_fft:
+        near_ach = near_fft_flops(n, L, p) / (stage_ms["p2p_l2p"] / 1000.0) / 1e12
+        roof_near = {"kernel": "k_nz_fwd + k_nz_mac + k_nz_inv (near zone by FFT, L2P fused; the whole stage)",
+                     "bound": "alu", "achieved": near_ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": near_ach / fp32_peak, "traffic": NEAR_FFT_TRAFFIC.get((n, L, p)),
+                     "traffic_source": NEAR_FFT_TRAFFIC_SOURCE if NEAR_FFT_TRAFFIC.get((n, L, p)) else None,
+                     "peak_source": "measured (of measured): " + fma["how"]}
+    else:
+        p2p_ach = p2p_flops(n, L) / (stage_ms["p2p_l2p"] / 1000.0) / 1e12
+        traffic = P2P_TRAFFIC.get((n, L, p))
+        roof_p2p = {"kernel": "k_p2p (fused L2P + near-zone sum)", "bound": "alu", "achieved": p2p_ach,
+                    "peak": fp32_peak, "unit": "TFLOP/s", "frac": p2p_ach / fp32_peak,
+                    "traffic": traffic, "traffic_source": P2P_TRAFFIC_SOURCE if traffic else None,
+                    "peak_source": "measured (of measured): " + fma["how"], "fp32_probe": fma}
     roof_m2l = None
-    if tc_levels:
-        tc_ms = sum(stage_ms[f"m2l_level{lev}"] for lev in tc_levels)
-        alg = sum(2.0 * 4 * p ** 3 * p ** 3 * 189 * 8 ** lev for lev in tc_levels)
+    if tc:
+        # the leaf level's launch: the longest single launch of the mixed forms
+        tc_ms = stage_ms[f"m2l_level{L}"]
+        alg = 2.0 * 4 * p ** 3 * p ** 3 * 189 * 8 ** L
         ach = alg / (tc_ms / 1000.0) / 1e12
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        roof_m2l = {"kernel": "k_m2l_tc (levels " + ",".join(map(str, tc_levels)) + ")", "bound": "tensor",
-                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+        traffic = M2L_TC_TRAFFIC.get((n, L, p))
+        roof_m2l = {"kernel": f"k_m2l_tc (level {L}, one launch)", "bound": "tensor",
+                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
+                    "traffic_source": M2L_TC_TRAFFIC_SOURCE if traffic else None,
                     "executed_tflops": ach * (3 if prec == B.FMM_PREC_BF16X3 else 1),
-                    "peak_source": f"bf16_tflops_sustained ({src}); achieved counts the algorithmic contraction, "
-                                   "bf16x3 executes 3 MMAs per product"}
-    roof = roof_p2p if (dominant == "p2p_l2p" or roof_m2l is None) else roof_m2l
+                    "executed_frac": ach * (3 if prec == B.FMM_PREC_BF16X3 else 1) / peak,
+                    "peak_source": f"bf16_tflops_sustained ({src}, of measured); achieved counts the algorithmic "
+                                   "contraction (2 x 4p^3 x p^3 x 189 flop per node), bf16x3 executes 3 MMAs per "
+                                   "product"}
+    if near_fft:
+        roof = roof_m2l if roof_m2l is not None else roof_near
+    else:
+        roof = roof_p2p if (dominant == "p2p_l2p" or roof_m2l is None) else roof_m2l
 
     # end to end through the public host-buffer entry point
     hin = torch.from_numpy(rho_host).pin_memory()
@@ -524,11 +601,12 @@ def run_ours(args):
         "wall_s": wall,
         "roofline": roof,
         "roofline_p2p": roof_p2p,
+        "roofline_near_fft": roof_near,
         "roofline_m2l": roof_m2l,
         "e2e": {"value": ws * n ** 3 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * n ** 3,
                 "d2h_bytes_per_step": 16 * n ** 3},
-        "gpu_launches": launches_per_solve(L, tc, p) * args.steps,
-        "solve_roofline": solve_roofline(n, L, p, tc, ms, peaks, fp32_peak),
+        "gpu_launches": launches_per_solve(L, tc, p, near_fft) * args.steps,
+        "solve_roofline": solve_roofline(n, L, p, tc, ms, peaks, fp32_peak, near_fft),
         "clocks": clocks,
         "error_statement": statement,
         "device_checks": checks,
@@ -536,6 +614,8 @@ def run_ours(args):
     if plain is not None:
         line["plain_fp32"] = plain
         line["speedup_vs_plain_fp32"] = plain["ms_per_step"] / ms
+    if forms:
+        line["forms"] = forms
     if host_leg:
         line["cpu_baseline"] = cpu_baseline()
         refs = pm_references(rho_host)
@@ -663,6 +743,9 @@ def main():
                     help="weights (.npz with 'w') of the learned table correction for the mixed form; "
                          "default: the trained order-6 weights shipped with the package, when p = 6")
     ap.add_argument("--no-correction", action="store_true", help="time the mixed form without the correction")
+    ap.add_argument("--near", choices=["fft", "direct"], default="fft",
+                    help="near zone of the timed form: FFT convolution on the doubled grid (Sec. 3; 8-cell "
+                         "leaves) or the direct sum; the plain FP32 form always uses the direct sum")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

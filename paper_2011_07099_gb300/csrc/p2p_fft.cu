@@ -134,9 +134,12 @@ __global__ void __launch_bounds__(kThr) k_nz_kernel(const float4* __restrict__ n
 // Source spectra: CTA per leaf; masses m = (rho - mean) / N^3 (mean as hi + lo,
 // as in the direct kernel) zero-padded to M^3.  Writes m^[chunk][leaf][32];
 // the slot after the last leaf is the all-zero spectrum of an out-of-box
-// neighbour (isolated problem), cleared at allocation.
-__global__ void __launch_bounds__(kThr) k_nz_fwd(const float* __restrict__ rho, const double* __restrict__ mean, int N,
-                                                int L, float2* __restrict__ Mhat) {
+// neighbour (isolated problem), cleared at allocation.  Each pass gives a
+// thread whole lines: the line's nonzero inputs in registers, the twiddles in
+// registers at compile-time indices.
+constexpr int kFwdThr = kNM * kNX;           // 144: one thread per (ky, kx) line of the last pass
+__global__ void __launch_bounds__(kFwdThr) k_nz_fwd(const float* __restrict__ rho, const double* __restrict__ mean,
+                                                   int N, int L, float2* __restrict__ Mhat) {
   __shared__ float2 w[kNM];
   __shared__ float m[kNS * kNS * kNS];
   __shared__ float2 A[kNS * kNS * kNX];    // [z][y][kx]
@@ -155,33 +158,51 @@ __global__ void __launch_bounds__(kThr) k_nz_fwd(const float* __restrict__ rho, 
     m[i] = ((r - mu_hi) - mu_lo) * inv_vol;
   }
   __syncthreads();
-  for (int i = tid; i < kNS * kNS * kNX; i += blockDim.x) {     // x: 8 real inputs -> kx in [0, M/2]
-    const int kx = i % kNX, zy = i / kNX;
-    float2 acc = make_float2(0.f, 0.f);
+  float2 tw[kNM];
 #pragma unroll
-    for (int x = 0; x < kNS; ++x) {
-      const float v = m[zy * kNS + x];
-      const float2 t = w[(kx * x) % kNM];
-      acc.x = fmaf(v, t.x, acc.x);
-      acc.y = fmaf(v, t.y, acc.y);
+  for (int j = 0; j < kNM; ++j) tw[j] = w[j];
+  if (tid < kNS * kNS) {                     // x: line (z, y), 8 real inputs -> kx in [0, M/2]
+    float v[kNS];
+#pragma unroll
+    for (int x = 0; x < kNS; ++x) v[x] = m[tid * kNS + x];
+#pragma unroll
+    for (int kx = 0; kx < kNX; ++kx) {
+      float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int x = 0; x < kNS; ++x) {
+        a.x = fmaf(v[x], tw[(kx * x) % kNM].x, a.x);
+        a.y = fmaf(v[x], tw[(kx * x) % kNM].y, a.y);
+      }
+      A[tid * kNX + kx] = a;
     }
-    A[i] = acc;
   }
   __syncthreads();
-  for (int i = tid; i < kNS * kNM * kNX; i += blockDim.x) {     // y: 8 nonzero inputs -> 16
-    const int kx = i % kNX, ky = (i / kNX) % kNM, z = i / (kNX * kNM);
-    float2 acc = make_float2(0.f, 0.f);
+  if (tid < kNS * kNX) {                     // y: line (z, kx), 8 nonzero inputs -> 16
+    const int kx = tid % kNX, z = tid / kNX;
+    float2 v[kNS];
 #pragma unroll
-    for (int y = 0; y < kNS; ++y) cfma(acc, A[(z * kNS + y) * kNX + kx], w[(ky * y) % kNM]);
-    B[i] = acc;
+    for (int y = 0; y < kNS; ++y) v[y] = A[(z * kNS + y) * kNX + kx];
+#pragma unroll
+    for (int ky = 0; ky < kNM; ++ky) {
+      float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int y = 0; y < kNS; ++y) cfma(a, v[y], tw[(ky * y) % kNM]);
+      B[(z * kNM + ky) * kNX + kx] = a;
+    }
   }
   __syncthreads();
-  for (int k = tid; k < kNK; k += blockDim.x) {                 // z: 8 nonzero inputs -> 16
-    const int kxy = k % (kNX * kNM), kz = k / (kNX * kNM);
-    float2 acc = make_float2(0.f, 0.f);
+  {                                          // z: line (ky, kx), 8 nonzero inputs -> 16
+    float2 v[kNS];
 #pragma unroll
-    for (int z = 0; z < kNS; ++z) cfma(acc, B[z * kNM * kNX + kxy], w[(kz * z) % kNM]);
-    Mhat[((size_t)(k / kNC) * (nl3 + 1) + leaf) * kNC + k % kNC] = acc;
+    for (int z = 0; z < kNS; ++z) v[z] = B[z * kNM * kNX + tid];
+#pragma unroll
+    for (int kz = 0; kz < kNM; ++kz) {
+      float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int z = 0; z < kNS; ++z) cfma(a, v[z], tw[(kz * z) % kNM]);
+      const int k = kz * kNM * kNX + tid;
+      Mhat[((size_t)(k / kNC) * (nl3 + 1) + leaf) * kNC + k % kNC] = a;
+    }
   }
 }
 
@@ -253,7 +274,7 @@ __global__ void __launch_bounds__(kThr, 2) k_nz_mac(const float2* __restrict__ K
 
 // Shared-memory carve-up of the inverse kernel (floats), for order p.
 struct NzInvSmem {
-  int w8, far, in, t1, t2, spec, zb, yb, total;
+  int w8, far, in, t1, t2, spec, total;
   __host__ __device__ NzInvSmem(int p) {
     const int p3 = p * p * p;
     w8 = 0;                                           // p S float2
@@ -261,18 +282,22 @@ struct NzInvSmem {
     in = far + 4 * kNS * kNS * kNS;                   // 4 p^3 floats
     t1 = in + 4 * p3;                                 // 4 p p S floats
     t2 = t1 + 4 * p * p * kNS;                        // 4 p S S floats
-    spec = (t2 + 4 * p * kNS * kNS + 3) / 4 * 4;      // M^2 (M/2+1) float2
-    zb = spec + 2 * kNK;                              // S M (M/2+1) float2
-    yb = zb + 2 * kNS * kNM * kNX;                    // S S (M/2+1) float2
-    total = yb + 2 * kNS * kNS * kNX;
+    spec = (t2 + 4 * p * kNS * kNS + 3) / 4 * 4;      // 4 fields x M^2 (M/2+1) float2
+    total = spec + 4 * 2 * kNK;
   }
 };
+constexpr int kInvThr = 288;                 // 576 z lines, 288 y lines, 256 x lines of the 4 fields
 
 // Inverse transforms of one target leaf's 4 field spectra (only the S^3
 // cells of the leaf are formed), plus the L2P far field; writes the results.
-__global__ void __launch_bounds__(kThr) k_nz_inv(const float2* __restrict__ Phat, int N, int L, int p,
-                                                const float* __restrict__ Fleaf, const float2* __restrict__ wp2m,
-                                                float* __restrict__ phi, float* __restrict__ acc_out) {
+// The four spectra arrive by cp.async while the L2P runs.  Each pass works in
+// place: a thread holds a whole line's inputs in registers and writes its 8
+// kept outputs over the line's first 8 slots, so the z pass leaves
+// [f][z < 8][ky][kx] and the y pass [f][z][y < 8][kx] (stride M*(M/2+1)).
+__global__ void __launch_bounds__(kInvThr, 2) k_nz_inv(const float2* __restrict__ Phat, int N, int L, int p,
+                                                      const float* __restrict__ Fleaf,
+                                                      const float2* __restrict__ wp2m, float* __restrict__ phi,
+                                                      float* __restrict__ acc_out) {
   __shared__ float2 w[kNM];
   extern __shared__ float4 sm4[];
   float* base = reinterpret_cast<float*>(sm4);
@@ -281,67 +306,80 @@ __global__ void __launch_bounds__(kThr) k_nz_inv(const float2* __restrict__ Phat
   float* far = base + lay.far;
   float* in = base + lay.in;
   float2* spec = reinterpret_cast<float2*>(base + lay.spec);
-  float2* Z = reinterpret_cast<float2*>(base + lay.zb);
-  float2* Y = reinterpret_cast<float2*>(base + lay.yb);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const unsigned leaf = blockIdx.x;
   const int p3 = p * p * p;
   const size_t N3 = (size_t)N * N * N;
+  {
+    const float2* src = Phat + (size_t)leaf * 4 * kNK;
+    for (int i = tid; i < 4 * kNK / 2; i += nthr) tc::cp_async16(tc::smem_u32(spec + 2 * i), src + 2 * i, 16u);
+    tc::cp_async_commit();
+  }
   twiddles(w, tid);
   for (int i = tid; i < p * kNS; i += nthr) W8[i] = wp2m[i];
-  const float* src = Fleaf + (size_t)leaf * 4 * p3;
-  for (int i = tid; i < 4 * p3; i += nthr) in[i] = __ldg(src + i);
+  const float* fsrc = Fleaf + (size_t)leaf * 4 * p3;
+  for (int i = tid; i < 4 * p3; i += nthr) in[i] = __ldg(fsrc + i);
   __syncthreads();
   // L2P: far[f][cz][cy][cx] = sum_s l_s(cz) l_s(cy) l_s(cx) F[f][s] (ends with a barrier)
   contract3(in, base + lay.t1, base + lay.t2, far, 4, p, kNS, W8, kNS, true, tid, nthr);
+  float2 tw[kNM];                              // conj twiddles: e^{+2 pi i j / M}
+#pragma unroll
+  for (int j = 0; j < kNM; ++j) tw[j] = make_float2(w[j].x, -w[j].y);
+  tc::cp_async_wait<0>();
+  __syncthreads();
+  constexpr int PL = kNM * kNX;                // one kz (or z) plane of a field: 144 values
+  for (int u = tid; u < 4 * PL; u += nthr) {   // z: line (f, ky, kx), 16 -> the 8 kept planes
+    float2* line = spec + (u / PL) * kNK + u % PL;
+    float2 v[kNM];
+#pragma unroll
+    for (int kz = 0; kz < kNM; ++kz) v[kz] = line[kz * PL];
+#pragma unroll
+    for (int z = 0; z < kNS; ++z) {
+      float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int kz = 0; kz < kNM; ++kz) cfma(a, v[kz], tw[(kz * z) % kNM]);
+      line[z * PL] = a;
+    }
+  }
+  __syncthreads();
+  for (int u = tid; u < 4 * kNS * kNX; u += nthr) {   // y: line (f, z, kx), 16 -> the 8 kept rows
+    const int kx = u % kNX, z = (u / kNX) % kNS, f = u / (kNX * kNS);
+    float2* line = spec + f * kNK + z * PL + kx;
+    float2 v[kNM];
+#pragma unroll
+    for (int ky = 0; ky < kNM; ++ky) v[ky] = line[ky * kNX];
+#pragma unroll
+    for (int y = 0; y < kNS; ++y) {
+      float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int ky = 0; ky < kNM; ++ky) cfma(a, v[ky], tw[(ky * y) % kNM]);
+      line[y * kNX] = a;
+    }
+  }
+  __syncthreads();
   uint32_t lx, ly, lz;
   unmorton(leaf, lx, ly, lz);
   const float scale = 1.f / (float)(kNM * kNM * kNM);
-  for (int q = 0; q < 4; ++q) {
-    const float4* s4 = reinterpret_cast<const float4*>(Phat + ((size_t)leaf * 4 + q) * kNK);
-    float4* d4 = reinterpret_cast<float4*>(spec);
-    for (int i = tid; i < kNK / 2; i += nthr) d4[i] = __ldg(s4 + i);
-    __syncthreads();
-    for (int i = tid; i < kNS * kNM * kNX; i += nthr) {      // z: 16 -> the 8 kept planes
-      const int kxy = i % (kNX * kNM), z = i / (kNX * kNM);
-      float2 a = make_float2(0.f, 0.f);
+  for (int u = tid; u < 4 * kNS * kNS; u += nthr) {   // x: line (f, z, y), half spectrum -> 8 real cells
+    const int y = u % kNS, z = (u / kNS) % kNS, f = u / (kNS * kNS);
+    const float2* line = spec + f * kNK + z * PL + y * kNX;
+    float2 v[kNX];
 #pragma unroll
-      for (int kz = 0; kz < kNM; ++kz) {
-        const float2 t = w[(kz * z) % kNM];
-        cfma(a, spec[kz * kNM * kNX + kxy], make_float2(t.x, -t.y));
-      }
-      Z[i] = a;
-    }
-    __syncthreads();
-    for (int i = tid; i < kNS * kNS * kNX; i += nthr) {      // y: 16 -> the 8 kept rows
-      const int kx = i % kNX, y = (i / kNX) % kNS, z = i / (kNX * kNS);
-      float2 a = make_float2(0.f, 0.f);
+    for (int kx = 0; kx < kNX; ++kx) v[kx] = line[kx];
+    const size_t o = ((size_t)(lz * kNS + z) * N + (ly * kNS + y)) * N + lx * kNS;
+    float* dst = f == 0 ? phi + o : acc_out + (size_t)(f - 1) * N3 + o;
+    const float* fr = far + f * kNS * kNS * kNS + (z * kNS + y) * kNS;
 #pragma unroll
-      for (int ky = 0; ky < kNM; ++ky) {
-        const float2 t = w[(ky * y) % kNM];
-        cfma(a, Z[(z * kNM + ky) * kNX + kx], make_float2(t.x, -t.y));
-      }
-      Y[i] = a;
-    }
-    __syncthreads();
-    for (int i = tid; i < kNS * kNS * kNS; i += nthr) {      // x: half spectrum -> 8 real cells
-      const int x = i % kNS, zy = i / kNS;
-      const float2* yr = Y + zy * kNX;
-      float v = 0.f;
+    for (int x = 0; x < kNS; ++x) {
+      float r = 0.f;                             // Re(v e^{+i theta}) = v.x cos - v.y sin
 #pragma unroll
       for (int kx = 1; kx < kNX - 1; ++kx) {
-        const float2 t = w[(kx * x) % kNM];            // Re(Y e^{+i theta}) = Y.x cos + Y.y (-sin)
-        v = fmaf(yr[kx].x, t.x, v);
-        v = fmaf(yr[kx].y, t.y, v);
+        r = fmaf(v[kx].x, tw[(kx * x) % kNM].x, r);
+        r = fmaf(-v[kx].y, tw[(kx * x) % kNM].y, r);
       }
-      v = 2.f * v + yr[0].x + ((x & 1) ? -yr[kNX - 1].x : yr[kNX - 1].x);
-      const int y = zy % kNS, z = zy / kNS;
-      const size_t o = ((size_t)(lz * kNS + z) * N + (ly * kNS + y)) * N + lx * kNS + x;
-      const float r = v * scale + far[q * kNS * kNS * kNS + i];
-      if (q == 0) phi[o] = r;
-      else acc_out[(size_t)(q - 1) * N3 + o] = r;
+      r = 2.f * r + v[0].x + ((x & 1) ? -v[kNX - 1].x : v[kNX - 1].x);
+      dst[x] = r * scale + fr[x];
     }
-    __syncthreads();
   }
 }
 
@@ -375,11 +413,11 @@ cudaError_t launch_near_fft_kernels(Plan& P, cudaStream_t s) {
 cudaError_t launch_near_fft(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s) {
   const unsigned nl3 = 1u << (3 * P.L);
   const int nt = (1 << P.L) / kNT;
-  k_nz_fwd<<<nl3, kThr, 0, s>>>(rho, P.d_mean, P.N, P.L, P.nz_M);
+  k_nz_fwd<<<nl3, kFwdThr, 0, s>>>(rho, P.d_mean, P.N, P.L, P.nz_M);
   k_nz_mac<<<dim3(nt * nt * nt, kNCH), kThr, sizeof(float2) * (kNO * 4 * kNC + kNH * kNH * kNH * kNC), s>>>(
       P.nz_K, P.nz_M, P.nz_P, P.L, P.iso);
-  k_nz_inv<<<nl3, kThr, sizeof(float) * NzInvSmem(P.p).total, s>>>(P.nz_P, P.N, P.L, P.p, P.F[P.L], P.w_p2m, phi,
-                                                                  acc);
+  k_nz_inv<<<nl3, kInvThr, sizeof(float) * NzInvSmem(P.p).total, s>>>(P.nz_P, P.N, P.L, P.p, P.F[P.L], P.w_p2m,
+                                                                     phi, acc);
   return cudaGetLastError();
 }
 
