@@ -64,14 +64,16 @@ __device__ __forceinline__ void twiddles(float2* w, int tid) {
 
 // The kernel's value for field f at lag d (cells), from the folded near table
 // (|d_i| in [0, 2S-1]); the gradient fields take the sign of their own
-// component as the direct sum does.
+// component as the direct sum does, and vanish where that component is 0
+// (the table holds exact zeros there for G_S1 and G_0), so that every field
+// is exactly even (Phi) or odd (g) under d -> -d.
 __device__ __forceinline__ double near_value(const float4* __restrict__ tab, int f, int dx, int dy, int dz) {
   constexpr int TD = 2 * kNS;
   const int ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy, az = dz < 0 ? -dz : dz;
   const float4 t = __ldg(tab + (az * TD + ay) * TD + ax);
   switch (f) {
     case 0: return (double)t.x;
-    case 1: return dx >= 0 ? (double)t.y : -(double)t.y;
+    case 1: return dx > 0 ? (double)t.y : (dx < 0 ? -(double)t.y : 0.0);
     case 2: return dy > 0 ? (double)t.z : (dy < 0 ? -(double)t.z : 0.0);
     default: return dz > 0 ? (double)t.w : (dz < 0 ? -(double)t.w : 0.0);
   }
@@ -206,69 +208,119 @@ __global__ void __launch_bounds__(kFwdThr) k_nz_fwd(const float* __restrict__ rh
   }
 }
 
-// Spectral sums: CTA (tile of 4^3 target leaves, chunk c).  Thread (g, f):
-// frequency c*32 + f of the 8 target leaves of group g (a 4 x 2 x 1 slab),
-// 4 fields each.
-__global__ void __launch_bounds__(kThr, 2) k_nz_mac(const float2* __restrict__ Khat, const float2* __restrict__ Mhat,
+// Spectral sums: CTA (tile of 4^3 target leaves, 8 consecutive chunks of 32
+// frequencies).  Thread (g, f): frequency f of the chunk for the 8 target
+// leaves of group g (a 4 x 2 x 1 slab), 4 fields each.  The next chunk's
+// kernel and source spectra are copied (cp.async) while the current one is
+// summed.  The kernels are real and Phi's is even, g's odd, under lag ->
+// -lag, so K^_{-o} = s conj(K^_o) (s = +1 for Phi, -1 for g) and the 26
+// non-central offsets are taken in pairs (o, -o): with M+ = m^_{T+o},
+// M- = m^_{T-o}, K^_o = a + ib,
+//   K^_o M+ + s conj(K^_o) M- = a (M+ + s M-) + i b (M+ - s M-).
+constexpr int kCPC = 8;                      // chunks per CTA
+constexpr int kMacStage = kNO * 4 * kNC + kNH * kNH * kNH * kNC;   // float2 per pipeline stage
+static_assert(kNCH % kCPC == 0, "chunk groups");
+__global__ void __launch_bounds__(kThr, 1) k_nz_mac(const float2* __restrict__ Khat, const float2* __restrict__ Mhat,
                                                    float2* __restrict__ Phat, int L, int iso) {
   extern __shared__ float4 sm4[];
-  float2* sK = reinterpret_cast<float2*>(sm4);          // [o][f][32]
-  float2* sM = sK + kNO * 4 * kNC;                      // [halo leaf][32]
+  unsigned* hleaf = reinterpret_cast<unsigned*>(sm4);             // [216] source leaf of each halo slot
+  float2* stage0 = reinterpret_cast<float2*>(sm4) + 128;           // 1 KB after the halo list
   const int tid = threadIdx.x;
   const int nl = 1 << L, nt = nl / kNT;
   const unsigned nl3 = 1u << (3 * L);
-  const int t = blockIdx.x, c = blockIdx.y;
+  const int t = blockIdx.x, c0 = blockIdx.y * kCPC;
   const int TX = t % nt, TY = (t / nt) % nt, TZ = t / (nt * nt);
-  {
-    const float2* src = Khat + (size_t)c * kNO * 4 * kNC;
-    for (int i = tid; i < kNO * 4 * kNC / 2; i += blockDim.x)
+  if (tid < kNH * kNH * kNH) {
+    const int hx = tid % kNH, hy = (tid / kNH) % kNH, hz = tid / (kNH * kNH);
+    int gx = TX * kNT + hx - 1, gy = TY * kNT + hy - 1, gz = TZ * kNT + hz - 1;
+    if (iso && (gx < 0 || gy < 0 || gz < 0 || gx >= nl || gy >= nl || gz >= nl)) {
+      hleaf[tid] = nl3;                                            // the all-zero spectrum
+    } else {
+      gx = (gx + nl) % nl;
+      gy = (gy + nl) % nl;
+      gz = (gz + nl) % nl;
+      hleaf[tid] = morton((uint32_t)gx, (uint32_t)gy, (uint32_t)gz);
+    }
+  }
+  __syncthreads();
+  auto load = [&](int c, int st) {
+    float2* sK = stage0 + st * kMacStage;
+    float2* sM = sK + kNO * 4 * kNC;
+    const float2* src = Khat + (size_t)c * kNO * 4 * kNC;          // offsets 0..13 (the rest by symmetry)
+    for (int i = tid; i < (kNO / 2 + 1) * 4 * kNC / 2; i += blockDim.x)
       tc::cp_async16(tc::smem_u32(sK + 2 * i), src + 2 * i, 16u);
+    const float2* msrc = Mhat + (size_t)c * (nl3 + 1) * kNC;
     for (int i = tid; i < kNH * kNH * kNH * (kNC / 2); i += blockDim.x) {
       const int h = i / (kNC / 2), q = i % (kNC / 2);
-      const int hx = h % kNH, hy = (h / kNH) % kNH, hz = h / (kNH * kNH);
-      int gx = TX * kNT + hx - 1, gy = TY * kNT + hy - 1, gz = TZ * kNT + hz - 1;
-      unsigned leaf;
-      if (iso && (gx < 0 || gy < 0 || gz < 0 || gx >= nl || gy >= nl || gz >= nl)) {
-        leaf = nl3;                                     // the all-zero spectrum
-      } else {
-        gx = (gx + nl) % nl;
-        gy = (gy + nl) % nl;
-        gz = (gz + nl) % nl;
-        leaf = morton((uint32_t)gx, (uint32_t)gy, (uint32_t)gz);
-      }
-      tc::cp_async16(tc::smem_u32(sM + h * kNC + 2 * q), Mhat + ((size_t)c * (nl3 + 1) + leaf) * kNC + 2 * q, 16u);
+      tc::cp_async16(tc::smem_u32(sM + h * kNC + 2 * q), msrc + (size_t)hleaf[h] * kNC + 2 * q, 16u);
     }
     tc::cp_async_commit();
-    tc::cp_async_wait<0>();
-    __syncthreads();
-  }
+  };
   const int f = tid % kNC, g = tid / kNC;
   const int hbase = 2 * (g & 1) * kNH + (g >> 1) * kNH * kNH;   // halo index of the group's first leaf, less (1,1,1)
-  float2 acc[8][4];
+  load(c0, 0);
+  for (int it = 0; it < kCPC; ++it) {
+    const int c = c0 + it;
+    if (it + 1 < kCPC) {
+      load(c + 1, (it + 1) & 1);
+      tc::cp_async_wait<1>();
+    } else {
+      tc::cp_async_wait<0>();
+    }
+    __syncthreads();
+    const float2* sK = stage0 + (it & 1) * kMacStage;
+    const float2* sM = sK + kNO * 4 * kNC;
+    float2 acc[8][4];
+    {                                                 // the central offset
+      float2 k[4];
 #pragma unroll
-  for (int j = 0; j < 8; ++j)
+      for (int q = 0; q < 4; ++q) k[q] = sK[(13 * 4 + q) * kNC + f];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[j][q] = make_float2(0.f, 0.f);
+      for (int j = 0; j < 8; ++j) {
+        const int h = hbase + ((j & 3) + 1) + kNH * ((j >> 2) + 1) + kNH * kNH;
+        const float2 mv = sM[h * kNC + f];
 #pragma unroll
-  for (int o = 0; o < kNO; ++o) {
-    const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
-    float2 k[4];
+        for (int q = 0; q < 4; ++q) {
+          acc[j][q] = make_float2(0.f, 0.f);
+          cfma(acc[j][q], k[q], mv);
+        }
+      }
+    }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) k[q] = sK[(o * 4 + q) * kNC + f];
+    for (int o = 0; o < 13; ++o) {                    // pairs (o, 26 - o): offsets -(ox,oy,oz) and +(ox,oy,oz)
+      const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+      float2 k[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) k[q] = sK[(o * 4 + q) * kNC + f];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int hp = hbase + ((j & 3) + ox + 1) + kNH * ((j >> 2) + oy + 1) + kNH * kNH * (oz + 1);
+        const int hm = hbase + ((j & 3) - ox + 1) + kNH * ((j >> 2) - oy + 1) + kNH * kNH * (-oz + 1);
+        const float2 mp = sM[hp * kNC + f], mm = sM[hm * kNC + f];
+        const float2 sum = make_float2(mp.x + mm.x, mp.y + mm.y), dif = make_float2(mp.x - mm.x, mp.y - mm.y);
+        float2& a0 = acc[j][0];
+        a0.x = fmaf(k[0].x, sum.x, a0.x);
+        a0.x = fmaf(-k[0].y, dif.y, a0.x);
+        a0.y = fmaf(k[0].x, sum.y, a0.y);
+        a0.y = fmaf(k[0].y, dif.x, a0.y);
+#pragma unroll
+        for (int q = 1; q < 4; ++q) {
+          float2& a = acc[j][q];
+          a.x = fmaf(k[q].x, dif.x, a.x);
+          a.x = fmaf(-k[q].y, sum.y, a.x);
+          a.y = fmaf(k[q].x, dif.y, a.y);
+          a.y = fmaf(k[q].y, sum.x, a.y);
+        }
+      }
+    }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int h = hbase + ((j & 3) + ox + 1) + kNH * ((j >> 2) + oy + 1) + kNH * kNH * (oz + 1);
-      const float2 mv = sM[h * kNC + f];
+      const uint32_t lx = TX * kNT + (j & 3), ly = TY * kNT + 2 * (g & 1) + (j >> 2), lz = TZ * kNT + (g >> 1);
+      const size_t leaf = morton(lx, ly, lz);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) cfma(acc[j][q], k[q], mv);
+      for (int q = 0; q < 4; ++q) Phat[(leaf * 4 + q) * kNK + (size_t)c * kNC + f] = acc[j][q];
     }
-  }
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const uint32_t lx = TX * kNT + (j & 3), ly = TY * kNT + 2 * (g & 1) + (j >> 2), lz = TZ * kNT + (g >> 1);
-    const size_t leaf = morton(lx, ly, lz);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) Phat[(leaf * 4 + q) * kNK + (size_t)c * kNC + f] = acc[j][q];
+    __syncthreads();                                  // this stage is refilled two chunks on
   }
 }
 
@@ -399,7 +451,7 @@ cudaError_t setup_near_fft(const Plan& P) {
                                        (int)(2 * sizeof(double2) * kNM * kNM * kNX));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_nz_mac, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(float2) * (kNO * 4 * kNC + kNH * kNH * kNH * kNC)));
+                           (int)(sizeof(float2) * (128 + 2 * kMacStage)));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_nz_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(sizeof(float) * NzInvSmem(kMaxOrder).total));
@@ -414,7 +466,7 @@ cudaError_t launch_near_fft(Plan& P, const float* rho, float* phi, float* acc, c
   const unsigned nl3 = 1u << (3 * P.L);
   const int nt = (1 << P.L) / kNT;
   k_nz_fwd<<<nl3, kFwdThr, 0, s>>>(rho, P.d_mean, P.N, P.L, P.nz_M);
-  k_nz_mac<<<dim3(nt * nt * nt, kNCH), kThr, sizeof(float2) * (kNO * 4 * kNC + kNH * kNH * kNH * kNC), s>>>(
+  k_nz_mac<<<dim3(nt * nt * nt, kNCH / kCPC), kThr, sizeof(float2) * (128 + 2 * kMacStage), s>>>(
       P.nz_K, P.nz_M, P.nz_P, P.L, P.iso);
   k_nz_inv<<<nl3, kInvThr, sizeof(float) * NzInvSmem(P.p).total, s>>>(P.nz_P, P.N, P.L, P.p, P.F[P.L], P.w_p2m,
                                                                      phi, acc);
