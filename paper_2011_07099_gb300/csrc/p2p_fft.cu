@@ -324,29 +324,127 @@ __global__ void __launch_bounds__(kThr, 1) k_nz_mac(const float2* __restrict__ K
   }
 }
 
-// Shared-memory carve-up of the inverse kernel (floats), for order p.
+// Complex helpers of the inverse transforms.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 mul_i(float2 a) { return make_float2(-a.y, a.x); }
+
+// 4-point inverse DFT, y_z = sum_m x_m e^{+2 pi i m z / 4}.
+__device__ __forceinline__ void idft4(float2 x0, float2 x1, float2 x2, float2 x3, float2 (&y)[4]) {
+  const float2 c0 = cadd(x0, x2), c1 = csub(x0, x2), d0 = cadd(x1, x3), d1 = mul_i(csub(x1, x3));
+  y[0] = cadd(c0, d0);
+  y[2] = csub(c0, d0);
+  y[1] = cadd(c1, d1);
+  y[3] = csub(c1, d1);
+}
+// 8-point inverse DFT of x[0], x[s], ..., x[7s] by one radix-2 split into two
+// 4-point transforms; t1 = e^{+2 pi i / 8}, t3 = e^{+6 pi i / 8}.
+template <int OFF, int STRIDE>
+__device__ __forceinline__ void idft8(const float2 (&x)[16], float2 (&y)[8], float2 t1, float2 t3) {
+  float2 a[4], b[4];
+  idft4(x[OFF], x[OFF + 2 * STRIDE], x[OFF + 4 * STRIDE], x[OFF + 6 * STRIDE], a);
+  idft4(x[OFF + STRIDE], x[OFF + 3 * STRIDE], x[OFF + 5 * STRIDE], x[OFF + 7 * STRIDE], b);
+  const float2 b1 = cmul(b[1], t1), b2 = mul_i(b[2]), b3 = cmul(b[3], t3);
+  y[0] = cadd(a[0], b[0]);
+  y[4] = csub(a[0], b[0]);
+  y[1] = cadd(a[1], b1);
+  y[5] = csub(a[1], b1);
+  y[2] = cadd(a[2], b2);
+  y[6] = csub(a[2], b2);
+  y[3] = cadd(a[3], b3);
+  y[7] = csub(a[3], b3);
+}
+// Outputs 0..7 of the 16-point inverse DFT of v (decimation in time: the
+// 8-point transforms E, O of the even and odd samples, X_z = E_z + t^z O_z);
+// tw[j] = e^{+2 pi i j / 16}.
+__device__ __forceinline__ void idft16_first_half(const float2 (&v)[16], float2 (&out)[8], const float2 (&tw)[kNM]) {
+  float2 E[8], O[8];
+  idft8<0, 2>(v, E, tw[2], tw[6]);
+  idft8<1, 2>(v, O, tw[2], tw[6]);
+  out[0] = cadd(E[0], O[0]);
+  out[4] = cadd(E[4], mul_i(O[4]));
+#pragma unroll
+  for (int z = 1; z < 8; ++z)
+    if (z != 4) out[z] = cadd(E[z], cmul(tw[z], O[z]));
+}
+
+// L2P of one 8-cell leaf: far[f][cz][cy][cx] = sum_s l_s(cz) l_s(cy) l_s(cx)
+// F[f][s], as the separable contraction of the direct kernel (x, then y, then
+// z; each output the FP32 sum over the gridlet points of the hi weights plus
+// that of the lo weights, in the same order, so the far field is bitwise the
+// direct kernel's), with the indices taken apart by shifts.  t1: 4 p p 8,
+// t2: 4 p 8 8 floats.  Ends with a barrier.
+__device__ __forceinline__ void l2p8(const float* __restrict__ F, float* __restrict__ t1, float* __restrict__ t2,
+                                     float* __restrict__ far, const float2* __restrict__ W8, int p, int tid,
+                                     int nthr) {
+  for (int i = tid; i < 4 * p * p * kNS; i += nthr) {        // x: line (f, sz, sy)
+    const float* src = F + (i >> 3) * p;
+    const int cx = i & 7;
+    float acc = 0.f, lo = 0.f;
+    for (int k = 0; k < p; ++k) {
+      const float2 w8 = W8[k * kNS + cx];
+      acc = fmaf(w8.x, src[k], acc);
+      lo = fmaf(w8.y, src[k], lo);
+    }
+    t1[i] = acc + lo;
+  }
+  __syncthreads();
+  for (int i = tid; i < 4 * p * kNS * kNS; i += nthr) {      // y: line (f, sz, cx)
+    const int cx = i & 7, cy = (i >> 3) & 7;
+    const float* src = t1 + (i >> 6) * p * kNS + cx;
+    float acc = 0.f, lo = 0.f;
+    for (int k = 0; k < p; ++k) {
+      const float2 w8 = W8[k * kNS + cy];
+      acc = fmaf(w8.x, src[k * kNS], acc);
+      lo = fmaf(w8.y, src[k * kNS], lo);
+    }
+    t2[i] = acc + lo;
+  }
+  __syncthreads();
+  for (int i = tid; i < 4 * kNS * kNS * kNS; i += nthr) {    // z: line (f, cy, cx)
+    const int cyx = i & 63, cz = (i >> 6) & 7;
+    const float* src = t2 + (i >> 9) * p * kNS * kNS + cyx;
+    float acc = 0.f, lo = 0.f;
+    for (int k = 0; k < p; ++k) {
+      const float2 w8 = W8[k * kNS + cz];
+      acc = fmaf(w8.x, src[k * kNS * kNS], acc);
+      lo = fmaf(w8.y, src[k * kNS * kNS], lo);
+    }
+    far[i] = acc + lo;
+  }
+  __syncthreads();
+}
+
+// Shared-memory carve-up of the inverse kernel (floats), for order p: two
+// pipeline stages of (4 field spectra, the leaf's local field).
 struct NzInvSmem {
-  int w8, far, in, t1, t2, spec, total;
+  int w8, far, t1, t2, in0, in1, spec0, spec1, total;
   __host__ __device__ NzInvSmem(int p) {
     const int p3 = p * p * p;
     w8 = 0;                                           // p S float2
     far = (2 * p * kNS + 3) / 4 * 4;                  // 4 S^3 floats
-    in = far + 4 * kNS * kNS * kNS;                   // 4 p^3 floats
-    t1 = in + 4 * p3;                                 // 4 p p S floats
+    t1 = far + 4 * kNS * kNS * kNS;                   // 4 p p S floats
     t2 = t1 + 4 * p * p * kNS;                        // 4 p S S floats
-    spec = (t2 + 4 * p * kNS * kNS + 3) / 4 * 4;      // 4 fields x M^2 (M/2+1) float2
-    total = spec + 4 * 2 * kNK;
+    in0 = (t2 + 4 * p * kNS * kNS + 3) / 4 * 4;       // 4 p^3 floats (a multiple of 4)
+    in1 = in0 + 4 * p3;
+    spec0 = in1 + 4 * p3;                             // 4 fields x M^2 (M/2+1) float2
+    spec1 = spec0 + 4 * 2 * kNK;
+    total = spec1 + 4 * 2 * kNK;
   }
 };
-constexpr int kInvThr = 288;                 // 576 z lines, 288 y lines, 256 x lines of the 4 fields
+constexpr int kInvThr = 576;                 // one thread per z line of the 4 fields (288 y, 256 x lines)
 
-// Inverse transforms of one target leaf's 4 field spectra (only the S^3
-// cells of the leaf are formed), plus the L2P far field; writes the results.
-// The four spectra arrive by cp.async while the L2P runs.  Each pass works in
-// place: a thread holds a whole line's inputs in registers and writes its 8
-// kept outputs over the line's first 8 slots, so the z pass leaves
-// [f][z < 8][ky][kx] and the y pass [f][z][y < 8][kx] (stride M*(M/2+1)).
-__global__ void __launch_bounds__(kInvThr, 2) k_nz_inv(const float2* __restrict__ Phat, int N, int L, int p,
+// Inverse transforms of the target leaves' 4 field spectra (only the S^3
+// cells of a leaf are formed), plus the L2P far field; writes the results.
+// Persistent: a CTA walks the leaves blockIdx.x, + gridDim.x, ...; the next
+// leaf's spectra and local field arrive by cp.async while the current one is
+// transformed.  Each pass works in place: a thread holds a whole line in
+// registers and writes its 8 kept outputs over the line's first 8 slots, so
+// the z pass leaves [f][z < 8][ky][kx] and the y pass [f][z][y < 8][kx].
+__global__ void __launch_bounds__(kInvThr, 1) k_nz_inv(const float2* __restrict__ Phat, int N, int L, int p,
                                                       const float* __restrict__ Fleaf,
                                                       const float2* __restrict__ wp2m, float* __restrict__ phi,
                                                       float* __restrict__ acc_out) {
@@ -356,82 +454,85 @@ __global__ void __launch_bounds__(kInvThr, 2) k_nz_inv(const float2* __restrict_
   const NzInvSmem lay(p);
   float2* W8 = reinterpret_cast<float2*>(base + lay.w8);
   float* far = base + lay.far;
-  float* in = base + lay.in;
-  float2* spec = reinterpret_cast<float2*>(base + lay.spec);
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const unsigned leaf = blockIdx.x;
+  const unsigned nl3 = 1u << (3 * L);
   const int p3 = p * p * p;
   const size_t N3 = (size_t)N * N * N;
-  {
+  auto fetch = [&](unsigned leaf, int b) {
+    float2* spec = reinterpret_cast<float2*>(base + (b ? lay.spec1 : lay.spec0));
+    float* in = base + (b ? lay.in1 : lay.in0);
     const float2* src = Phat + (size_t)leaf * 4 * kNK;
     for (int i = tid; i < 4 * kNK / 2; i += nthr) tc::cp_async16(tc::smem_u32(spec + 2 * i), src + 2 * i, 16u);
+    const float* fsrc = Fleaf + (size_t)leaf * 4 * p3;
+    for (int i = tid; i < p3; i += nthr) tc::cp_async16(tc::smem_u32(in + 4 * i), fsrc + 4 * i, 16u);
     tc::cp_async_commit();
-  }
+  };
   twiddles(w, tid);
   for (int i = tid; i < p * kNS; i += nthr) W8[i] = wp2m[i];
-  const float* fsrc = Fleaf + (size_t)leaf * 4 * p3;
-  for (int i = tid; i < 4 * p3; i += nthr) in[i] = __ldg(fsrc + i);
+  unsigned leaf = blockIdx.x;
+  if (leaf < nl3) fetch(leaf, 0);
   __syncthreads();
-  // L2P: far[f][cz][cy][cx] = sum_s l_s(cz) l_s(cy) l_s(cx) F[f][s] (ends with a barrier)
-  contract3(in, base + lay.t1, base + lay.t2, far, 4, p, kNS, W8, kNS, true, tid, nthr);
-  float2 tw[kNM];                              // conj twiddles: e^{+2 pi i j / M}
+  float2 tw[kNM];                              // e^{+2 pi i j / M}
 #pragma unroll
   for (int j = 0; j < kNM; ++j) tw[j] = make_float2(w[j].x, -w[j].y);
-  tc::cp_async_wait<0>();
-  __syncthreads();
-  constexpr int PL = kNM * kNX;                // one kz (or z) plane of a field: 144 values
-  for (int u = tid; u < 4 * PL; u += nthr) {   // z: line (f, ky, kx), 16 -> the 8 kept planes
-    float2* line = spec + (u / PL) * kNK + u % PL;
-    float2 v[kNM];
-#pragma unroll
-    for (int kz = 0; kz < kNM; ++kz) v[kz] = line[kz * PL];
-#pragma unroll
-    for (int z = 0; z < kNS; ++z) {
-      float2 a = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int kz = 0; kz < kNM; ++kz) cfma(a, v[kz], tw[(kz * z) % kNM]);
-      line[z * PL] = a;
-    }
-  }
-  __syncthreads();
-  for (int u = tid; u < 4 * kNS * kNX; u += nthr) {   // y: line (f, z, kx), 16 -> the 8 kept rows
-    const int kx = u % kNX, z = (u / kNX) % kNS, f = u / (kNX * kNS);
-    float2* line = spec + f * kNK + z * PL + kx;
-    float2 v[kNM];
-#pragma unroll
-    for (int ky = 0; ky < kNM; ++ky) v[ky] = line[ky * kNX];
-#pragma unroll
-    for (int y = 0; y < kNS; ++y) {
-      float2 a = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int ky = 0; ky < kNM; ++ky) cfma(a, v[ky], tw[(ky * y) % kNM]);
-      line[y * kNX] = a;
-    }
-  }
-  __syncthreads();
-  uint32_t lx, ly, lz;
-  unmorton(leaf, lx, ly, lz);
   const float scale = 1.f / (float)(kNM * kNM * kNM);
-  for (int u = tid; u < 4 * kNS * kNS; u += nthr) {   // x: line (f, z, y), half spectrum -> 8 real cells
-    const int y = u % kNS, z = (u / kNS) % kNS, f = u / (kNS * kNS);
-    const float2* line = spec + f * kNK + z * PL + y * kNX;
-    float2 v[kNX];
-#pragma unroll
-    for (int kx = 0; kx < kNX; ++kx) v[kx] = line[kx];
-    const size_t o = ((size_t)(lz * kNS + z) * N + (ly * kNS + y)) * N + lx * kNS;
-    float* dst = f == 0 ? phi + o : acc_out + (size_t)(f - 1) * N3 + o;
-    const float* fr = far + f * kNS * kNS * kNS + (z * kNS + y) * kNS;
-#pragma unroll
-    for (int x = 0; x < kNS; ++x) {
-      float r = 0.f;                             // Re(v e^{+i theta}) = v.x cos - v.y sin
-#pragma unroll
-      for (int kx = 1; kx < kNX - 1; ++kx) {
-        r = fmaf(v[kx].x, tw[(kx * x) % kNM].x, r);
-        r = fmaf(-v[kx].y, tw[(kx * x) % kNM].y, r);
-      }
-      r = 2.f * r + v[0].x + ((x & 1) ? -v[kNX - 1].x : v[kNX - 1].x);
-      dst[x] = r * scale + fr[x];
+  constexpr int PL = kNM * kNX;                // one kz (or z) plane of a field: 144 values
+  for (int b = 0; leaf < nl3; leaf += gridDim.x, b ^= 1) {
+    if (leaf + gridDim.x < nl3) {
+      fetch(leaf + gridDim.x, b ^ 1);
+      tc::cp_async_wait<1>();
+    } else {
+      tc::cp_async_wait<0>();
     }
+    __syncthreads();
+    float2* spec = reinterpret_cast<float2*>(base + (b ? lay.spec1 : lay.spec0));
+    // L2P: far[f][cz][cy][cx] = sum_s l_s(cz) l_s(cy) l_s(cx) F[f][s] (ends with a barrier)
+    l2p8(base + (b ? lay.in1 : lay.in0), base + lay.t1, base + lay.t2, far, W8, p, tid, nthr);
+    for (int u = tid; u < 4 * PL; u += nthr) {   // z: line (f, ky, kx), 16 -> the 8 kept planes
+      float2* line = spec + (u / PL) * kNK + u % PL;
+      float2 v[kNM], o[kNS];
+#pragma unroll
+      for (int kz = 0; kz < kNM; ++kz) v[kz] = line[kz * PL];
+      idft16_first_half(v, o, tw);
+#pragma unroll
+      for (int z = 0; z < kNS; ++z) line[z * PL] = o[z];
+    }
+    __syncthreads();
+    for (int u = tid; u < 4 * kNS * kNX; u += nthr) {   // y: line (f, z, kx), 16 -> the 8 kept rows
+      const int kx = u % kNX, z = (u / kNX) % kNS, f = u / (kNX * kNS);
+      float2* line = spec + f * kNK + z * PL + kx;
+      float2 v[kNM], o[kNS];
+#pragma unroll
+      for (int ky = 0; ky < kNM; ++ky) v[ky] = line[ky * kNX];
+      idft16_first_half(v, o, tw);
+#pragma unroll
+      for (int y = 0; y < kNS; ++y) line[y * kNX] = o[y];
+    }
+    __syncthreads();
+    uint32_t lx, ly, lz;
+    unmorton(leaf, lx, ly, lz);
+    for (int u = tid; u < 4 * kNS * kNS; u += nthr) {   // x: line (f, z, y), half spectrum -> 8 real cells
+      const int y = u % kNS, z = (u / kNS) % kNS, f = u / (kNS * kNS);
+      const float2* line = spec + f * kNK + z * PL + y * kNX;
+      float2 v[kNX];
+#pragma unroll
+      for (int kx = 0; kx < kNX; ++kx) v[kx] = line[kx];
+      const size_t o = ((size_t)(lz * kNS + z) * N + (ly * kNS + y)) * N + lx * kNS;
+      float* dst = f == 0 ? phi + o : acc_out + (size_t)(f - 1) * N3 + o;
+      const float* fr = far + f * kNS * kNS * kNS + (z * kNS + y) * kNS;
+#pragma unroll
+      for (int x = 0; x < kNS; ++x) {
+        float r = 0.f;                             // Re(v e^{+i theta}) = v.x cos - v.y sin
+#pragma unroll
+        for (int kx = 1; kx < kNX - 1; ++kx) {
+          r = fmaf(v[kx].x, tw[(kx * x) % kNM].x, r);
+          r = fmaf(-v[kx].y, tw[(kx * x) % kNM].y, r);
+        }
+        r = 2.f * r + v[0].x + ((x & 1) ? -v[kNX - 1].x : v[kNX - 1].x);
+        dst[x] = r * scale + fr[x];
+      }
+    }
+    __syncthreads();     // spec, far and the local field are refilled or rewritten next
   }
 }
 
@@ -468,8 +569,9 @@ cudaError_t launch_near_fft(Plan& P, const float* rho, float* phi, float* acc, c
   k_nz_fwd<<<nl3, kFwdThr, 0, s>>>(rho, P.d_mean, P.N, P.L, P.nz_M);
   k_nz_mac<<<dim3(nt * nt * nt, kNCH / kCPC), kThr, sizeof(float2) * (128 + 2 * kMacStage), s>>>(
       P.nz_K, P.nz_M, P.nz_P, P.L, P.iso);
-  k_nz_inv<<<nl3, kInvThr, sizeof(float) * NzInvSmem(P.p).total, s>>>(P.nz_P, P.N, P.L, P.p, P.F[P.L], P.w_p2m,
-                                                                     phi, acc);
+  const unsigned inv_grid = nl3 < (unsigned)P.num_sms ? nl3 : (unsigned)P.num_sms;
+  k_nz_inv<<<inv_grid, kInvThr, sizeof(float) * NzInvSmem(P.p).total, s>>>(P.nz_P, P.N, P.L, P.p, P.F[P.L],
+                                                                          P.w_p2m, phi, acc);
   return cudaGetLastError();
 }
 
