@@ -371,104 +371,136 @@ __device__ __forceinline__ void idft16_first_half(const float2 (&v)[16], float2 
     if (z != 4) out[z] = cadd(E[z], cmul(tw[z], O[z]));
 }
 
-// L2P of one 8-cell leaf: far[f][cz][cy][cx] = sum_s l_s(cz) l_s(cy) l_s(cx)
-// F[f][s], as the separable contraction of the direct kernel (x, then y, then
-// z; each output the FP32 sum over the gridlet points of the hi weights plus
-// that of the lo weights, in the same order, so the far field is bitwise the
-// direct kernel's), with the indices taken apart by shifts.  t1: 4 p p 8,
-// t2: 4 p 8 8 floats.  Ends with a barrier.
-__device__ __forceinline__ void l2p8(const float* __restrict__ F, float* __restrict__ t1, float* __restrict__ t2,
-                                     float* __restrict__ far, const float2* __restrict__ W8, int p, int tid,
-                                     int nthr) {
-  for (int i = tid; i < 4 * p * p * kNS; i += nthr) {        // x: line (f, sz, sy)
-    const float* src = F + (i >> 3) * p;
-    const int cx = i & 7;
-    float acc = 0.f, lo = 0.f;
-    for (int k = 0; k < p; ++k) {
-      const float2 w8 = W8[k * kNS + cx];
-      acc = fmaf(w8.x, src[k], acc);
-      lo = fmaf(w8.y, src[k], lo);
+// L2P of the 8-cell leaves: far[f][cz][cy][cx] = sum_s l_s(cz) l_s(cy)
+// l_s(cx) F[f][s], as the separable contraction of the direct kernel (x, then
+// y, then z; each output the FP32 sum over the gridlet points of the hi
+// weights plus that of the lo weights, in the same order, so the far field is
+// bitwise the direct kernel's), written to the outputs; the inverse
+// transforms add the near field to it.  CTA per leaf; a thread takes whole
+// lines (the P inputs in registers, all 8 outputs), the P x 8 weight pairs in
+// registers.
+constexpr int kL2pThr = 128;
+template <int P>
+__global__ void __launch_bounds__(kL2pThr) k_nz_l2p(int N, const float* __restrict__ Fleaf,
+                                                   const float2* __restrict__ wp2m, float* __restrict__ phi,
+                                                   float* __restrict__ acc_out) {
+  __shared__ float F[4 * P * P * P];
+  __shared__ float t1[4 * P * P * kNS];
+  __shared__ float t2[4 * P * kNS * kNS];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const unsigned leaf = blockIdx.x;
+  const size_t N3 = (size_t)N * N * N;
+  float2 wr[P][kNS];
+#pragma unroll
+  for (int k = 0; k < P; ++k)
+#pragma unroll
+    for (int c = 0; c < kNS; ++c) wr[k][c] = __ldg(wp2m + k * kNS + c);
+  const float* src = Fleaf + (size_t)leaf * 4 * P * P * P;
+  for (int i = tid; i < 4 * P * P * P; i += nthr) F[i] = __ldg(src + i);
+  __syncthreads();
+  auto line8 = [&](const float (&in)[P], float (&out)[kNS]) {
+#pragma unroll
+    for (int c = 0; c < kNS; ++c) {
+      float acc = 0.f, lo = 0.f;
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        acc = fmaf(wr[k][c].x, in[k], acc);
+        lo = fmaf(wr[k][c].y, in[k], lo);
+      }
+      out[c] = acc + lo;
     }
-    t1[i] = acc + lo;
+  };
+  for (int l = tid; l < 4 * P * P; l += nthr) {              // x: line (f, sz, sy)
+    float in[P], out[kNS];
+#pragma unroll
+    for (int k = 0; k < P; ++k) in[k] = F[l * P + k];
+    line8(in, out);
+#pragma unroll
+    for (int c = 0; c < kNS; ++c) t1[l * kNS + c] = out[c];
   }
   __syncthreads();
-  for (int i = tid; i < 4 * p * kNS * kNS; i += nthr) {      // y: line (f, sz, cx)
-    const int cx = i & 7, cy = (i >> 3) & 7;
-    const float* src = t1 + (i >> 6) * p * kNS + cx;
-    float acc = 0.f, lo = 0.f;
-    for (int k = 0; k < p; ++k) {
-      const float2 w8 = W8[k * kNS + cy];
-      acc = fmaf(w8.x, src[k * kNS], acc);
-      lo = fmaf(w8.y, src[k * kNS], lo);
-    }
-    t2[i] = acc + lo;
+  for (int l = tid; l < 4 * P * kNS; l += nthr) {            // y: line (f, sz, cx)
+    const int cx = l % kNS, g = l / kNS;
+    float in[P], out[kNS];
+#pragma unroll
+    for (int k = 0; k < P; ++k) in[k] = t1[(g * P + k) * kNS + cx];
+    line8(in, out);
+#pragma unroll
+    for (int c = 0; c < kNS; ++c) t2[(g * kNS + c) * kNS + cx] = out[c];
   }
   __syncthreads();
-  for (int i = tid; i < 4 * kNS * kNS * kNS; i += nthr) {    // z: line (f, cy, cx)
-    const int cyx = i & 63, cz = (i >> 6) & 7;
-    const float* src = t2 + (i >> 9) * p * kNS * kNS + cyx;
-    float acc = 0.f, lo = 0.f;
-    for (int k = 0; k < p; ++k) {
-      const float2 w8 = W8[k * kNS + cz];
-      acc = fmaf(w8.x, src[k * kNS * kNS], acc);
-      lo = fmaf(w8.y, src[k * kNS * kNS], lo);
-    }
-    far[i] = acc + lo;
+  uint32_t lx, ly, lz;
+  unmorton(leaf, lx, ly, lz);
+  for (int l = tid; l < 4 * kNS * kNS; l += nthr) {          // z: line (f, cy, cx) -> the outputs
+    const int cyx = l % (kNS * kNS), f = l / (kNS * kNS);
+    float in[P], out[kNS];
+#pragma unroll
+    for (int k = 0; k < P; ++k) in[k] = t2[(f * P + k) * kNS * kNS + cyx];
+    line8(in, out);
+    float* dst = (f == 0 ? phi : acc_out + (size_t)(f - 1) * N3) +
+                 ((size_t)(lz * kNS) * N + (ly * kNS + cyx / kNS)) * N + lx * kNS + cyx % kNS;
+#pragma unroll
+    for (int c = 0; c < kNS; ++c) dst[(size_t)c * N * N] = out[c];
   }
-  __syncthreads();
 }
 
-// Shared-memory carve-up of the inverse kernel (floats), for order p: two
-// pipeline stages of (4 field spectra, the leaf's local field).
-struct NzInvSmem {
-  int w8, far, t1, t2, in0, in1, spec0, spec1, total;
-  __host__ __device__ NzInvSmem(int p) {
-    const int p3 = p * p * p;
-    w8 = 0;                                           // p S float2
-    far = (2 * p * kNS + 3) / 4 * 4;                  // 4 S^3 floats
-    t1 = far + 4 * kNS * kNS * kNS;                   // 4 p p S floats
-    t2 = t1 + 4 * p * p * kNS;                        // 4 p S S floats
-    in0 = (t2 + 4 * p * kNS * kNS + 3) / 4 * 4;       // 4 p^3 floats (a multiple of 4)
-    in1 = in0 + 4 * p3;
-    spec0 = in1 + 4 * p3;                             // 4 fields x M^2 (M/2+1) float2
-    spec1 = spec0 + 4 * 2 * kNK;
-    total = spec1 + 4 * 2 * kNK;
+template <int P>
+void launch_l2p_p(const Plan& Pl, float* phi, float* acc, cudaStream_t s) {
+  k_nz_l2p<P><<<1u << (3 * Pl.L), kL2pThr, 0, s>>>(Pl.N, Pl.F[Pl.L], Pl.w_p2m, phi, acc);
+}
+void launch_l2p(const Plan& Pl, float* phi, float* acc, cudaStream_t s) {
+  switch (Pl.p) {
+    case 1: launch_l2p_p<1>(Pl, phi, acc, s); break;
+    case 2: launch_l2p_p<2>(Pl, phi, acc, s); break;
+    case 3: launch_l2p_p<3>(Pl, phi, acc, s); break;
+    case 4: launch_l2p_p<4>(Pl, phi, acc, s); break;
+    case 5: launch_l2p_p<5>(Pl, phi, acc, s); break;
+    case 6: launch_l2p_p<6>(Pl, phi, acc, s); break;
+    case 7: launch_l2p_p<7>(Pl, phi, acc, s); break;
+    default: launch_l2p_p<8>(Pl, phi, acc, s); break;
   }
-};
+}
+
+// Shared-memory carve-up of the inverse kernel (floats): two pipeline stages
+// of (the 4 field spectra, the 4 x 64 rows of the leaf's outputs).
+constexpr int kInvSpec = 4 * 2 * kNK;                 // floats of one stage's spectra
+constexpr int kInvRows = 4 * kNS * kNS * kNS;         // floats of one stage's output rows
+constexpr int kInvSmemFloats = 2 * (kInvSpec + kInvRows);
 constexpr int kInvThr = 576;                 // one thread per z line of the 4 fields (288 y, 256 x lines)
 
 // Inverse transforms of the target leaves' 4 field spectra (only the S^3
-// cells of a leaf are formed), plus the L2P far field; writes the results.
-// Persistent: a CTA walks the leaves blockIdx.x, + gridDim.x, ...; the next
-// leaf's spectra and local field arrive by cp.async while the current one is
-// transformed.  Each pass works in place: a thread holds a whole line in
-// registers and writes its 8 kept outputs over the line's first 8 slots, so
-// the z pass leaves [f][z < 8][ky][kx] and the y pass [f][z][y < 8][kx].
-__global__ void __launch_bounds__(kInvThr, 1) k_nz_inv(const float2* __restrict__ Phat, int N, int L, int p,
-                                                      const float* __restrict__ Fleaf,
-                                                      const float2* __restrict__ wp2m, float* __restrict__ phi,
-                                                      float* __restrict__ acc_out) {
+// cells of a leaf are formed), added to the far field k_nz_l2p left in the
+// outputs.  Persistent: a CTA walks the leaves blockIdx.x, + gridDim.x, ...;
+// the next leaf's spectra and output rows arrive by cp.async while the
+// current one is transformed.  Each pass works in place: a thread holds a
+// whole line in registers and writes its 8 kept outputs over the line's
+// first 8 slots, so the z pass leaves [f][z < 8][ky][kx] and the y pass
+// [f][z][y < 8][kx].
+__global__ void __launch_bounds__(kInvThr, 1) k_nz_inv(const float2* __restrict__ Phat, int N, int L,
+                                                      float* __restrict__ phi, float* __restrict__ acc_out) {
   __shared__ float2 w[kNM];
   extern __shared__ float4 sm4[];
   float* base = reinterpret_cast<float*>(sm4);
-  const NzInvSmem lay(p);
-  float2* W8 = reinterpret_cast<float2*>(base + lay.w8);
-  float* far = base + lay.far;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const unsigned nl3 = 1u << (3 * L);
-  const int p3 = p * p * p;
   const size_t N3 = (size_t)N * N * N;
+  auto row_of = [&](unsigned leaf, int r) -> float* {   // output row r = (f, z, y) of a leaf
+    uint32_t lx, ly, lz;
+    unmorton(leaf, lx, ly, lz);
+    const int y = r & 7, z = (r >> 3) & 7, f = r >> 6;
+    const size_t o = ((size_t)(lz * kNS + z) * N + (ly * kNS + y)) * N + lx * kNS;
+    return (f == 0 ? phi : acc_out + (size_t)(f - 1) * N3) + o;
+  };
   auto fetch = [&](unsigned leaf, int b) {
-    float2* spec = reinterpret_cast<float2*>(base + (b ? lay.spec1 : lay.spec0));
-    float* in = base + (b ? lay.in1 : lay.in0);
+    float2* spec = reinterpret_cast<float2*>(base + b * (kInvSpec + kInvRows));
+    float* rows = base + b * (kInvSpec + kInvRows) + kInvSpec;
     const float2* src = Phat + (size_t)leaf * 4 * kNK;
     for (int i = tid; i < 4 * kNK / 2; i += nthr) tc::cp_async16(tc::smem_u32(spec + 2 * i), src + 2 * i, 16u);
-    const float* fsrc = Fleaf + (size_t)leaf * 4 * p3;
-    for (int i = tid; i < p3; i += nthr) tc::cp_async16(tc::smem_u32(in + 4 * i), fsrc + 4 * i, 16u);
+    for (int i = tid; i < kInvRows / 4; i += nthr)
+      tc::cp_async16(tc::smem_u32(rows + 4 * i), row_of(leaf, i >> 1) + 4 * (i & 1), 16u);
     tc::cp_async_commit();
   };
   twiddles(w, tid);
-  for (int i = tid; i < p * kNS; i += nthr) W8[i] = wp2m[i];
   unsigned leaf = blockIdx.x;
   if (leaf < nl3) fetch(leaf, 0);
   __syncthreads();
@@ -485,9 +517,8 @@ __global__ void __launch_bounds__(kInvThr, 1) k_nz_inv(const float2* __restrict_
       tc::cp_async_wait<0>();
     }
     __syncthreads();
-    float2* spec = reinterpret_cast<float2*>(base + (b ? lay.spec1 : lay.spec0));
-    // L2P: far[f][cz][cy][cx] = sum_s l_s(cz) l_s(cy) l_s(cx) F[f][s] (ends with a barrier)
-    l2p8(base + (b ? lay.in1 : lay.in0), base + lay.t1, base + lay.t2, far, W8, p, tid, nthr);
+    float2* spec = reinterpret_cast<float2*>(base + b * (kInvSpec + kInvRows));
+    const float* rows = base + b * (kInvSpec + kInvRows) + kInvSpec;
     for (int u = tid; u < 4 * PL; u += nthr) {   // z: line (f, ky, kx), 16 -> the 8 kept planes
       float2* line = spec + (u / PL) * kNK + u % PL;
       float2 v[kNM], o[kNS];
@@ -509,17 +540,14 @@ __global__ void __launch_bounds__(kInvThr, 1) k_nz_inv(const float2* __restrict_
       for (int y = 0; y < kNS; ++y) line[y * kNX] = o[y];
     }
     __syncthreads();
-    uint32_t lx, ly, lz;
-    unmorton(leaf, lx, ly, lz);
     for (int u = tid; u < 4 * kNS * kNS; u += nthr) {   // x: line (f, z, y), half spectrum -> 8 real cells
       const int y = u % kNS, z = (u / kNS) % kNS, f = u / (kNS * kNS);
       const float2* line = spec + f * kNK + z * PL + y * kNX;
       float2 v[kNX];
 #pragma unroll
       for (int kx = 0; kx < kNX; ++kx) v[kx] = line[kx];
-      const size_t o = ((size_t)(lz * kNS + z) * N + (ly * kNS + y)) * N + lx * kNS;
-      float* dst = f == 0 ? phi + o : acc_out + (size_t)(f - 1) * N3 + o;
-      const float* fr = far + f * kNS * kNS * kNS + (z * kNS + y) * kNS;
+      float* dst = row_of(leaf, u);
+      const float* fr = rows + u * kNS;
 #pragma unroll
       for (int x = 0; x < kNS; ++x) {
         float r = 0.f;                             // Re(v e^{+i theta}) = v.x cos - v.y sin
@@ -532,7 +560,7 @@ __global__ void __launch_bounds__(kInvThr, 1) k_nz_inv(const float2* __restrict_
         dst[x] = r * scale + fr[x];
       }
     }
-    __syncthreads();     // spec, far and the local field are refilled or rewritten next
+    __syncthreads();     // this stage is refilled two leaves on
   }
 }
 
@@ -555,7 +583,7 @@ cudaError_t setup_near_fft(const Plan& P) {
                            (int)(sizeof(float2) * (128 + 2 * kMacStage)));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_nz_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(sizeof(float) * NzInvSmem(kMaxOrder).total));
+                              (int)(sizeof(float) * kInvSmemFloats));
 }
 
 cudaError_t launch_near_fft_kernels(Plan& P, cudaStream_t s) {
@@ -569,9 +597,9 @@ cudaError_t launch_near_fft(Plan& P, const float* rho, float* phi, float* acc, c
   k_nz_fwd<<<nl3, kFwdThr, 0, s>>>(rho, P.d_mean, P.N, P.L, P.nz_M);
   k_nz_mac<<<dim3(nt * nt * nt, kNCH / kCPC), kThr, sizeof(float2) * (128 + 2 * kMacStage), s>>>(
       P.nz_K, P.nz_M, P.nz_P, P.L, P.iso);
+  launch_l2p(P, phi, acc, s);
   const unsigned inv_grid = nl3 < (unsigned)P.num_sms ? nl3 : (unsigned)P.num_sms;
-  k_nz_inv<<<inv_grid, kInvThr, sizeof(float) * NzInvSmem(P.p).total, s>>>(P.nz_P, P.N, P.L, P.p, P.F[P.L],
-                                                                          P.w_p2m, phi, acc);
+  k_nz_inv<<<inv_grid, kInvThr, sizeof(float) * kInvSmemFloats, s>>>(P.nz_P, P.N, P.L, phi, acc);
   return cudaGetLastError();
 }
 
