@@ -148,8 +148,9 @@ P2P_TRAFFIC = {(256, 5, 6): 419.3e6}
 M2L_TC_TRAFFIC = {(256, 5, 6): 1603.3e6}
 M2L_TC_TRAFFIC_SOURCE = ("ncu capture of the current k_m2l_tc at 256^3 p=6, level 5 (dram__bytes read 1503.1 MB + "
                          "write 100.2 MB), not measured in this run")
-NEAR_FFT_TRAFFIC = {}
-NEAR_FFT_TRAFFIC_SOURCE = "ncu capture of the current k_nz_fwd + k_nz_mac + k_nz_inv at 256^3 p=6"
+NEAR_FFT_TRAFFIC = {(256, 5, 6): 6989.5e6}
+NEAR_FFT_TRAFFIC_SOURCE = ("ncu capture of the current k_nz_fwd + k_nz_mac + k_nz_l2p + k_nz_inv at 256^3 p=6 "
+                           "(dram__bytes read+write summed), not measured in this run")
 P2P_TRAFFIC_SOURCE = ("ncu capture of the current k_p2p at 256^3 p=6 (dram__bytes read 197.6 MB + write 221.7 MB), "
                       "not measured in this run")
 
@@ -362,14 +363,14 @@ def device_check(B, plan):
 
 def launches_per_solve(L, tc, p=6, near_fft=False):
     # mean (2) + P2M + M2M per level + M2L per level + L2L per level + P2P
-    # (three kernels with the near zone by FFT: forward, sums, inverse + L2P);
+    # (four kernels with the near zone by FFT: forward, sums, L2P, inverse);
     # M2L of the coarse levels (2-3, and every level above the leaves at
     # order >= 7) adds the FP64 range-sum kernel, tensor-core levels the
     # BF16 split kernel
     wide = lambda lev: lev <= 3 or (p >= 7 and lev < L)
     tc_first = max(4, L) if p >= 7 else 4
     m2l = sum(2 if (wide(lev) or (tc and lev >= tc_first)) else 1 for lev in range(2, L + 1))
-    return 2 + 1 + (L - 2) + m2l + (L - 2) + (3 if near_fft else 1)
+    return 2 + 1 + (L - 2) + m2l + (L - 2) + (4 if near_fft else 1)
 
 
 def solve_roofline(n, L, p, tc, ms, peaks, fp32_tflops, near_fft=False):
@@ -539,7 +540,7 @@ def run_ours(args):
     roof_p2p = roof_near = None
     if near_fft:
         near_ach = near_fft_flops(n, L, p) / (stage_ms["p2p_l2p"] / 1000.0) / 1e12
-        roof_near = {"kernel": "k_nz_fwd + k_nz_mac + k_nz_inv (near zone by FFT, L2P fused; the whole stage)",
+        roof_near = {"kernel": "k_nz_fwd + k_nz_mac + k_nz_l2p + k_nz_inv (near zone by FFT and L2P; the whole stage)",
                      "bound": "alu", "achieved": near_ach, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": near_ach / fp32_peak, "traffic": NEAR_FFT_TRAFFIC.get((n, L, p)),
                      "traffic_source": NEAR_FFT_TRAFFIC_SOURCE if NEAR_FFT_TRAFFIC.get((n, L, p)) else None,
