@@ -8,11 +8,13 @@ if ROOT not in sys.path:
 
 
 def test_launch_count_claim_matches_the_profiled_launch_list():
-    # the ncu launch list of the 256^3 p = 6 bench (6 solves: 4 mixed, 2
-    # plain) counts per mixed solve: mean 2, P2M 1, M2M 3, M2L 8 (level 2
-    # double-float + range sum, level 3 split table + range sum, levels 4-5
-    # BF16 split + tensor core), L2L 3, P2P 1; the plain form replaces each
+    # the ncu launch list of the 256^3 p = 6 bench counts per solve of the
+    # headline form: mean 2, P2M 1, M2M 3, M2L 8 (level 2 double-float +
+    # range sum, level 3 split table + range sum, levels 4-5 BF16 split +
+    # tensor core), L2L 3, near zone by FFT 4 (forward, sums, L2P, inverse):
+    # 21; the direct near zone is 1 kernel, and the plain form replaces each
     # tensor-core pair by one FP32 kernel
     import bench
+    assert bench.launches_per_solve(5, True, 6, near_fft=True) == 21
     assert bench.launches_per_solve(5, True, 6) == 18
     assert bench.launches_per_solve(5, False, 6) == 16
