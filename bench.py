@@ -647,7 +647,14 @@ def run_batch(args):
     import tempfile
     os.environ.setdefault("FMM_AUTOTUNE_CACHE", os.path.join(tempfile.gettempdir(), "fmm_autotune.jsonl"))
     t0 = time.perf_counter()
-    batch = B.Batch(Ns, [0] * nf, ps, precision=B.FMM_PREC_BF16X3)
+    # with the near zone by FFT the fields whose N is 8 x a power of two take
+    # 8-cell leaves (its leaf size); the others are autotuned (L = 0)
+    near_fft = args.near == "fft"
+    Ls = [(n // 8).bit_length() - 1 if near_fft and n % 8 == 0 and (n // 8) & (n // 8 - 1) == 0 and n >= 32 else 0
+          for n in Ns]
+    batch = B.Batch(Ns, Ls, ps, precision=B.FMM_PREC_BF16X3)
+    if near_fft:
+        B.fmm_batch_set_near_algorithm(batch.handle, B.FMM_NEAR_FFT)
     tune_s = time.perf_counter() - t0
     d = [torch.from_numpy(inputs.lognormal(n, sigma=float(s_), seed=2000 + i)).cuda() for i, (n, s_) in
          enumerate(zip(Ns, sig))]
@@ -675,7 +682,8 @@ def run_batch(args):
     line = {"metric": "FMM cells/s, batch of 64 uneven periodic fields (one graph launch)", "value": cells / (ms / 1e3),
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
-            "config": {"workload": f"{nf} fields, N in {{32,48,64,96,128}}, p in {{4,6}}, lognormal sigma U[0.3,1.5]",
+            "config": {"workload": f"{nf} fields, N in {{32,48,64,96,128}}, p in {{4,6}}, lognormal sigma U[0.3,1.5]"
+                                   + (", near zone by FFT where the leaves hold 8 cells" if near_fft else ""),
                        "cells": cells, "levels": batch.levels, "N": Ns, "order": ps, "autotune_s": tune_s},
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
@@ -704,6 +712,8 @@ def run_full512(args):
             plan = B.Plan(n, L, p)
             if prec:
                 plan.set_precision(prec)
+            if prec != B.FMM_PREC_FP32 and args.near == "fft":
+                B.fmm_plan_set_near_algorithm(plan.handle, B.FMM_NEAR_FFT)   # the plain form keeps the direct sum
             phi = torch.empty((n, n, n), device=dev)
             acc = torch.empty((3, n, n, n), device=dev)
             ms, stage, _ = _time_solves(B, plan, rho, phi, acc, args.steps, max(1, args.warmup), l2_flush, stream,
@@ -720,7 +730,8 @@ def run_full512(args):
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": out["mixed_bf16x3"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
-            "config": {"workload": "512^3, p=8, L=6 (S=8), 1 + lognormal(sigma=1.5) + 4096 Plummer clumps",
+            "config": {"workload": "512^3, p=8, L=6 (S=8), 1 + lognormal(sigma=1.5) + 4096 Plummer clumps; mixed form: "
+                                   "bf16x3 leaf-level M2L" + (", near zone by FFT" if args.near == "fft" else ""),
                        "forms": out}, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     return 0

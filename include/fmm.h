@@ -268,6 +268,14 @@ fmm_batch* fmm_batch_create(int nfields, const int* N, const int* L, const int* 
 /* M2L arithmetic of every field (FMM_PREC_*). */
 int fmm_batch_set_precision(fmm_batch* batch, int mode);
 
+/* The near-zone algorithm (FMM_NEAR_DIRECT / FMM_NEAR_FFT, see
+ * fmm_plan_set_near_algorithm) of every field of the batch that supports it:
+ * with FMM_NEAR_FFT the fields with 8-cell leaves take the FFT form, the
+ * others keep the direct sum.  Allocates the fields' spectra (synchronous)
+ * and drops the captured graph (the next solve captures again).  FMM_ERR_ARG
+ * for an unknown value, FMM_ERR_ALLOC if the spectra do not fit. */
+int fmm_batch_set_near_algorithm(fmm_batch* batch, int algorithm);
+
 /* The leaf level chosen for each field (nfields ints). */
 int fmm_batch_get_levels(const fmm_batch* batch, int* L);
 

@@ -75,6 +75,7 @@ SIGNATURES = {
     "fmm_plan_set_green_mesh": (_I, [_VP, _FP, _SZ]),
     "fmm_plan_set_m2l_algorithm": (_I, [_VP, _I]),
     "fmm_plan_set_near_algorithm": (_I, [_VP, _I]),
+    "fmm_batch_set_near_algorithm": (_I, [_VP, _I]),
     "fmm_plan_set_table_grid": (_I, [_VP, _FP, _SZ]),
     "fmm_table_grid_grad": (_I, [_VP, _FP, _FP, _FP, ctypes.c_float, ctypes.c_float, _FP, _FP, _VP]),
     "fmm_probe_fma_flops": (ctypes.c_double, [_I, _I]),
@@ -242,6 +243,10 @@ def fmm_plan_set_m2l_algorithm(plan, algorithm):
 
 def fmm_plan_set_near_algorithm(plan, algorithm):
     _check(lib().fmm_plan_set_near_algorithm(plan, int(algorithm)), "fmm_plan_set_near_algorithm")
+
+
+def fmm_batch_set_near_algorithm(batch, algorithm):
+    _check(lib().fmm_batch_set_near_algorithm(batch, int(algorithm)), "fmm_batch_set_near_algorithm")
 
 
 def fmm_plan_set_green_mesh(plan, mesh):

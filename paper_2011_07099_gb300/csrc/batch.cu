@@ -270,6 +270,22 @@ int fmm_batch_set_precision(fmm_batch* b, int mode) {
   return fmm::set_last_error(FMM_OK);
 }
 
+int fmm_batch_set_near_algorithm(fmm_batch* b, int algorithm) {
+  if (!b || (algorithm != FMM_NEAR_DIRECT && algorithm != FMM_NEAR_FFT)) return fmm::set_last_error(FMM_ERR_ARG);
+  for (auto pl : b->plans) {
+    // the FFT near zone needs 8-cell leaves: other fields keep the direct sum
+    if (algorithm == FMM_NEAR_FFT && !fmm::near_fft_supported(*reinterpret_cast<const fmm::Plan*>(pl))) continue;
+    const int rc = fmm_plan_set_near_algorithm(pl, algorithm);
+    if (rc != FMM_OK) return rc;
+  }
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->sig.clear();
+  return fmm::set_last_error(FMM_OK);
+}
+
 int fmm_batch_get_levels(const fmm_batch* b, int* L) {
   if (!b || !L) return fmm::set_last_error(FMM_ERR_ARG);
   for (int i = 0; i < b->n; ++i) L[i] = b->L[i];

@@ -209,19 +209,41 @@ __global__ void __launch_bounds__(kFwdThr) k_nz_fwd(const float* __restrict__ rh
 }
 
 // Spectral sums: CTA (tile of 4^3 target leaves, 8 consecutive chunks of 32
-// frequencies).  Thread (g, f): frequency f of the chunk for the 8 target
-// leaves of group g (a 4 x 2 x 1 slab), 4 fields each.  The next chunk's
-// kernel and source spectra are copied (cp.async) while the current one is
-// summed.  The kernels are real and Phi's is even, g's odd, under lag ->
-// -lag, so K^_{-o} = s conj(K^_o) (s = +1 for Phi, -1 for g) and the 26
-// non-central offsets are taken in pairs (o, -o): with M+ = m^_{T+o},
-// M- = m^_{T-o}, K^_o = a + ib,
+// frequencies).  Thread (g, f): frequency f of the chunk for the 4 target
+// leaves of row g (x = 0..3 at y = g % 4, z = g / 4), 4 fields each.  The
+// next chunk's kernel and source spectra are copied (cp.async) while the
+// current one is summed.  The kernels are real and Phi's is even, g's odd,
+// under lag -> -lag, so K^_{-o} = s conj(K^_o) (s = +1 for Phi, -1 for g)
+// and the 26 non-central offsets are taken in pairs (o, -o): with
+// M+ = m^_{T+o}, M- = m^_{T-o}, K^_o = a + ib,
 //   K^_o M+ + s conj(K^_o) M- = a (M+ + s M-) + i b (M+ - s M-).
+// The pairs come in groups of the three x offsets: a group's 6 source spectra
+// of the +o row and 6 of the -o row are read once for its 3 x 4 pair terms.
 constexpr int kCPC = 8;                      // chunks per CTA
-constexpr int kMacStage = kNO * 4 * kNC + kNH * kNH * kNH * kNC;   // float2 per pipeline stage
+constexpr int kMacThr = 512;
+constexpr int kNKO = kNO / 2 + 1;            // kernel spectra used per chunk: offsets 0..13
+constexpr int kMacStage = kNKO * 4 * kNC + kNH * kNH * kNH * kNC;   // float2 per pipeline stage
 static_assert(kNCH % kCPC == 0, "chunk groups");
-__global__ void __launch_bounds__(kThr, 1) k_nz_mac(const float2* __restrict__ Khat, const float2* __restrict__ Mhat,
-                                                   float2* __restrict__ Phat, int L, int iso) {
+
+// one pair term for the 4 fields of one target leaf
+__device__ __forceinline__ void pair_term(float2 (&acc)[4], const float2 (&k)[4], float2 mp, float2 mm) {
+  const float2 sum = make_float2(mp.x + mm.x, mp.y + mm.y), dif = make_float2(mp.x - mm.x, mp.y - mm.y);
+  acc[0].x = fmaf(k[0].x, sum.x, acc[0].x);
+  acc[0].x = fmaf(-k[0].y, dif.y, acc[0].x);
+  acc[0].y = fmaf(k[0].x, sum.y, acc[0].y);
+  acc[0].y = fmaf(k[0].y, dif.x, acc[0].y);
+#pragma unroll
+  for (int q = 1; q < 4; ++q) {
+    acc[q].x = fmaf(k[q].x, dif.x, acc[q].x);
+    acc[q].x = fmaf(-k[q].y, sum.y, acc[q].x);
+    acc[q].y = fmaf(k[q].x, dif.y, acc[q].y);
+    acc[q].y = fmaf(k[q].y, sum.x, acc[q].y);
+  }
+}
+
+__global__ void __launch_bounds__(kMacThr, 1) k_nz_mac(const float2* __restrict__ Khat,
+                                                      const float2* __restrict__ Mhat, float2* __restrict__ Phat,
+                                                      int L, int iso) {
   extern __shared__ float4 sm4[];
   unsigned* hleaf = reinterpret_cast<unsigned*>(sm4);             // [216] source leaf of each halo slot
   float2* stage0 = reinterpret_cast<float2*>(sm4) + 128;           // 1 KB after the halo list
@@ -245,9 +267,9 @@ __global__ void __launch_bounds__(kThr, 1) k_nz_mac(const float2* __restrict__ K
   __syncthreads();
   auto load = [&](int c, int st) {
     float2* sK = stage0 + st * kMacStage;
-    float2* sM = sK + kNO * 4 * kNC;
+    float2* sM = sK + kNKO * 4 * kNC;
     const float2* src = Khat + (size_t)c * kNO * 4 * kNC;          // offsets 0..13 (the rest by symmetry)
-    for (int i = tid; i < (kNO / 2 + 1) * 4 * kNC / 2; i += blockDim.x)
+    for (int i = tid; i < kNKO * 4 * kNC / 2; i += blockDim.x)
       tc::cp_async16(tc::smem_u32(sK + 2 * i), src + 2 * i, 16u);
     const float2* msrc = Mhat + (size_t)c * (nl3 + 1) * kNC;
     for (int i = tid; i < kNH * kNH * kNH * (kNC / 2); i += blockDim.x) {
@@ -257,7 +279,9 @@ __global__ void __launch_bounds__(kThr, 1) k_nz_mac(const float2* __restrict__ K
     tc::cp_async_commit();
   };
   const int f = tid % kNC, g = tid / kNC;
-  const int hbase = 2 * (g & 1) * kNH + (g >> 1) * kNH * kNH;   // halo index of the group's first leaf, less (1,1,1)
+  const int ly = g % kNT, lz = g / kNT;
+  // halo slot of (x, y, z) in [0, 6)^3, frequency f
+  auto slot = [&](int x, int y, int z) { return ((z * kNH + y) * kNH + x) * kNC + f; };
   load(c0, 0);
   for (int it = 0; it < kCPC; ++it) {
     const int c = c0 + it;
@@ -269,16 +293,15 @@ __global__ void __launch_bounds__(kThr, 1) k_nz_mac(const float2* __restrict__ K
     }
     __syncthreads();
     const float2* sK = stage0 + (it & 1) * kMacStage;
-    const float2* sM = sK + kNO * 4 * kNC;
-    float2 acc[8][4];
-    {                                                 // the central offset
+    const float2* sM = sK + kNKO * 4 * kNC;
+    float2 acc[4][4];
+    {                                                 // the central offset (index 13)
       float2 k[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) k[q] = sK[(13 * 4 + q) * kNC + f];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int h = hbase + ((j & 3) + 1) + kNH * ((j >> 2) + 1) + kNH * kNH;
-        const float2 mv = sM[h * kNC + f];
+      for (int j = 0; j < 4; ++j) {
+        const float2 mv = sM[slot(j + 1, ly + 1, lz + 1)];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           acc[j][q] = make_float2(0.f, 0.f);
@@ -286,37 +309,31 @@ __global__ void __launch_bounds__(kThr, 1) k_nz_mac(const float2* __restrict__ K
         }
       }
     }
+    // groups of pairs sharing (oy, oz): offset index o = (ox+1) + 3 (oy+1) + 9 (oz+1)
 #pragma unroll
-    for (int o = 0; o < 13; ++o) {                    // pairs (o, 26 - o): offsets -(ox,oy,oz) and +(ox,oy,oz)
-      const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
-      float2 k[4];
+    for (int grp = 0; grp < 5; ++grp) {
+      // grp 0..2: oz = -1, oy = grp - 1, ox in {-1, 0, 1}; grp 3: oz = 0, oy = -1, ox in {-1, 0, 1};
+      // grp 4: the single pair (-1, 0, 0)
+      const int oz = grp < 3 ? -1 : 0, oy = grp < 3 ? grp - 1 : (grp == 3 ? -1 : 0);
+      float2 mp[kNH], mm[kNH];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) k[q] = sK[(o * 4 + q) * kNC + f];
+      for (int x = 0; x < kNH; ++x) {
+        mp[x] = sM[slot(x, ly + oy + 1, lz + oz + 1)];
+        mm[x] = sM[slot(x, ly - oy + 1, lz - oz + 1)];
+      }
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int hp = hbase + ((j & 3) + ox + 1) + kNH * ((j >> 2) + oy + 1) + kNH * kNH * (oz + 1);
-        const int hm = hbase + ((j & 3) - ox + 1) + kNH * ((j >> 2) - oy + 1) + kNH * kNH * (-oz + 1);
-        const float2 mp = sM[hp * kNC + f], mm = sM[hm * kNC + f];
-        const float2 sum = make_float2(mp.x + mm.x, mp.y + mm.y), dif = make_float2(mp.x - mm.x, mp.y - mm.y);
-        float2& a0 = acc[j][0];
-        a0.x = fmaf(k[0].x, sum.x, a0.x);
-        a0.x = fmaf(-k[0].y, dif.y, a0.x);
-        a0.y = fmaf(k[0].x, sum.y, a0.y);
-        a0.y = fmaf(k[0].y, dif.x, a0.y);
+      for (int ox = -1; ox <= (grp == 4 ? -1 : 1); ++ox) {
+        const int o = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
+        float2 k[4];
 #pragma unroll
-        for (int q = 1; q < 4; ++q) {
-          float2& a = acc[j][q];
-          a.x = fmaf(k[q].x, dif.x, a.x);
-          a.x = fmaf(-k[q].y, sum.y, a.x);
-          a.y = fmaf(k[q].x, dif.y, a.y);
-          a.y = fmaf(k[q].y, sum.x, a.y);
-        }
+        for (int q = 0; q < 4; ++q) k[q] = sK[(o * 4 + q) * kNC + f];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) pair_term(acc[j], k, mp[j + ox + 1], mm[j - ox + 1]);
       }
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const uint32_t lx = TX * kNT + (j & 3), ly = TY * kNT + 2 * (g & 1) + (j >> 2), lz = TZ * kNT + (g >> 1);
-      const size_t leaf = morton(lx, ly, lz);
+    for (int j = 0; j < 4; ++j) {
+      const size_t leaf = morton(TX * kNT + j, TY * kNT + ly, TZ * kNT + lz);
 #pragma unroll
       for (int q = 0; q < 4; ++q) Phat[(leaf * 4 + q) * kNK + (size_t)c * kNC + f] = acc[j][q];
     }
@@ -595,7 +612,7 @@ cudaError_t launch_near_fft(Plan& P, const float* rho, float* phi, float* acc, c
   const unsigned nl3 = 1u << (3 * P.L);
   const int nt = (1 << P.L) / kNT;
   k_nz_fwd<<<nl3, kFwdThr, 0, s>>>(rho, P.d_mean, P.N, P.L, P.nz_M);
-  k_nz_mac<<<dim3(nt * nt * nt, kNCH / kCPC), kThr, sizeof(float2) * (128 + 2 * kMacStage), s>>>(
+  k_nz_mac<<<dim3(nt * nt * nt, kNCH / kCPC), kMacThr, sizeof(float2) * (128 + 2 * kMacStage), s>>>(
       P.nz_K, P.nz_M, P.nz_P, P.L, P.iso);
   launch_l2p(P, phi, acc, s);
   const unsigned inv_grid = nl3 < (unsigned)P.num_sms ? nl3 : (unsigned)P.num_sms;

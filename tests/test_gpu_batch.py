@@ -61,6 +61,34 @@ def test_batch_equals_single_solves(B, prec):
     batch.close()
 
 
+def test_batch_with_near_fft_equals_single_solves(B):
+    # fields with 8-cell leaves take the FFT near zone, the others keep the
+    # direct sum; the captured batch equals the single solves bit for bit
+    Ns = [32, 64, 48, 128, 64]
+    ps = [4, 6, 6, 4, 3]
+    Ls = [2, 3, 3, 4, 4]                            # S = 8, 8, 6, 8, 4
+    rhos = [inputs.lognormal(n, sigma=0.7, seed=40 + i) for i, n in enumerate(Ns)]
+    d = [torch.from_numpy(r).cuda() for r in rhos]
+    pots = [torch.empty((n, n, n), device="cuda") for n in Ns]
+    accs = [torch.empty((3, n, n, n), device="cuda") for n in Ns]
+    batch = B.Batch(Ns, Ls, ps, precision=B.FMM_PREC_BF16X3)
+    B.fmm_batch_set_near_algorithm(batch.handle, B.FMM_NEAR_FFT)
+    for _ in range(2):                              # capture, then replay
+        batch.solve(d, pots, accs)
+    torch.cuda.synchronize()
+    batch.check()
+    for i in range(len(Ns)):
+        plan = B.Plan(Ns[i], Ls[i], ps[i])
+        plan.set_precision(B.FMM_PREC_BF16X3)
+        if Ns[i] >> Ls[i] == 8:
+            B.fmm_plan_set_near_algorithm(plan.handle, B.FMM_NEAR_FFT)
+        phi, acc = plan.solve(d[i])
+        torch.cuda.synchronize()
+        assert torch.equal(phi, pots[i]) and torch.equal(acc, accs[i]), i
+        plan.close()
+    batch.close()
+
+
 def test_autotuner_picks_a_valid_level_and_caches_it(B, tmp_path):
     cache = str(tmp_path / "tune.jsonl")
     L, ms = B.fmm_autotune_levels(64, 4, B.FMM_PREC_BF16X3, cache)
