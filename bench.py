@@ -148,7 +148,7 @@ P2P_TRAFFIC = {(256, 5, 6): 419.3e6}
 M2L_TC_TRAFFIC = {(256, 5, 6): 1603.3e6}
 M2L_TC_TRAFFIC_SOURCE = ("ncu capture of the current k_m2l_tc at 256^3 p=6, level 5 (dram__bytes read 1503.1 MB + "
                          "write 100.2 MB), not measured in this run")
-NEAR_FFT_TRAFFIC = {(256, 5, 6): 6989.5e6}
+NEAR_FFT_TRAFFIC = {(256, 5, 6): 6942.5e6}
 NEAR_FFT_TRAFFIC_SOURCE = ("ncu capture of the current k_nz_fwd + k_nz_mac + k_nz_l2p + k_nz_inv at 256^3 p=6 "
                            "(dram__bytes read+write summed), not measured in this run")
 P2P_TRAFFIC_SOURCE = ("ncu capture of the current k_p2p at 256^3 p=6 (dram__bytes read 197.6 MB + write 221.7 MB), "
