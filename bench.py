@@ -731,7 +731,8 @@ def run_full512(args):
             "ms_per_step": out["mixed_bf16x3"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
             "config": {"workload": "512^3, p=8, L=6 (S=8), 1 + lognormal(sigma=1.5) + 4096 Plummer clumps; mixed form: "
-                                   "bf16x3 leaf-level M2L" + (", near zone by FFT" if args.near == "fft" else ""),
+                                   "bf16x3 leaf-level M2L, bf16x6 level 5 (FP64 fields), double-float levels 2-4"
+                                   + (", near zone by FFT" if args.near == "fft" else ""),
                        "forms": out}, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     return 0

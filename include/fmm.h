@@ -105,14 +105,18 @@ int fmm_solve_host(fmm_plan* plan, const float* density_host,
 
 /* Select the M2L arithmetic (FMM_PREC_*).  Takes effect at the next solve.
  * FMM_PREC_BF16 / FMM_PREC_BF16X3 apply to levels >= 4 (see
- * fmm_plan_set_tc_min_level; at order >= 7 only the leaf level).  In every
- * mode the coarse levels, whose long-range sums cancel most, run on the CUDA
- * cores in extended precision: level 2 in double-float (error-free products
- * and sums), level 3 with split tables, both reduced in FP64 into FP64 local
- * fields; at order >= 7 every level above the leaves does the same.  The
- * first tensor-core selection allocates and tabulates the split BF16 tables,
- * translation tiles and multipole buffers (synchronous).  Order 1 ignores
- * the tensor-core modes.  FMM_ERR_ARG for an unknown mode. */
+ * fmm_plan_set_tc_min_level).  In every mode the coarse levels, whose
+ * long-range sums cancel most, run on the CUDA cores in extended precision:
+ * level 2 in double-float (error-free products and sums), level 3 with split
+ * tables, both reduced in FP64 into FP64 local fields.  At order >= 7 every
+ * level above the leaves keeps FP64 local fields: in the tensor-core modes
+ * levels >= 5 of them run "bf16x6" (both operands split in three BF16 parts,
+ * six products, partials of each 32-deep stage added into a double-float
+ * total, written in FP64), the coarser ones the double-float CUDA-core
+ * kernel, and the leaf level the selected mode.  The first tensor-core
+ * selection allocates and tabulates the split BF16 tables, translation tiles
+ * and multipole buffers (synchronous).  Order 1 ignores the tensor-core
+ * modes.  FMM_ERR_ARG for an unknown mode. */
 int fmm_plan_set_precision(fmm_plan* plan, int mode);
 
 /* Boundary of the problem.  FMM_BOUNDARY_PERIODIC (default) is the natively
@@ -212,15 +216,19 @@ int fmm_plan_inject_fault(fmm_plan* plan, int kind);
 int fmm_plan_set_m2l_group(fmm_plan* plan, int offsets_per_partial);
 
 /* Mixed-precision forms: the first tree level whose M2L (eq. fmm2) runs on
- * the tensor cores; coarser levels run the FP32 CUDA-core kernel.  Default
- * and minimum 4 (levels 2 and 3 always use the extended-precision CUDA-core
- * kernels).  A value above the leaf level L keeps every level on the CUDA
- * cores.  At order >= 7 only the leaf level can run on the tensor cores: the
- * L2L interpolation to the children extrapolates beyond the parent gridlet
- * (absolute weight sums ~1100 at p = 8), so every level above the leaves
- * keeps FP64 local fields fed by compensated CUDA-core sums.  Lowering the
- * level after the first mixed-precision solve builds the translation tiles
- * of the new levels (synchronously).  FMM_ERR_ARG outside 4..9. */
+ * the tensor cores; coarser levels run the CUDA-core kernels.  Default and
+ * minimum 4 (levels 2 and 3 always use the extended-precision CUDA-core
+ * kernels); at order >= 7 the default is level 5 (or the leaf level, if
+ * coarser).  A value above the leaf level L keeps every level on the CUDA
+ * cores.  At order >= 7 the levels above the leaves keep FP64 local fields
+ * (the L2L interpolation to the children extrapolates beyond the parent
+ * gridlet: absolute weight sums ~1100 at p = 8) and those on the tensor
+ * cores run the bf16x6 mode (fmm_plan_set_precision); a level set here is
+ * taken as given, also at order >= 7 (measured on the 512^3 order-8
+ * clustered workload, bf16x6 at level 4 costs 6.1e-5 against the FP64
+ * oracle, at level 5 2.6e-6).  Lowering the level after the first
+ * mixed-precision solve builds the translation tiles of the new levels
+ * (synchronously).  FMM_ERR_ARG outside 4..9. */
 int fmm_plan_set_tc_min_level(fmm_plan* plan, int level);
 
 /* Synchronise the device and read the plan's device error word: FMM_OK, or

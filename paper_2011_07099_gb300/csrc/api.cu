@@ -176,7 +176,8 @@ int retabulate(Plan& P) {
   if (P.tc_ready) {
     for (int l = fmm::kTcMinLevel; l <= P.L; ++l) {
       if (!P.Apre[l]) continue;
-      if (fmm::launch_tab_bf16(P, l, 0) != cudaSuccess || fmm::launch_build_a(P, l, 0) != cudaSuccess)
+      if ((!fmm::tc_wide(P, l) && fmm::launch_tab_bf16(P, l, 0) != cudaSuccess) ||
+          fmm::launch_build_a(P, l, 0) != cudaSuccess)
         return FMM_ERR_CUDA;
     }
   }
@@ -371,11 +372,12 @@ int prepare_tc(Plan& P) {
   bool made = false;
   for (int l = fmm::tc_first_level(P); l <= P.L; ++l) {
     if (P.Apre[l]) continue;
-    if ((!P.tab_bf[l] && !dev_alloc(&P.tab_bf[l], E * E * E)) ||
-        (!P.Mbf_hi[l] && cudaMalloc(&P.Mbf_hi[l], fmm::tc_bsplit_bytes(P.p, l)) != cudaSuccess) ||
-        cudaMalloc(&P.Apre[l], fmm::tc_apre_bytes(P.p)) != cudaSuccess)
+    const bool wide = fmm::tc_wide(P, l);   // bf16x6: tiles from tab + tab_lo, no BF16 table
+    if ((!wide && !P.tab_bf[l] && !dev_alloc(&P.tab_bf[l], E * E * E)) ||
+        (!P.Mbf_hi[l] && cudaMalloc(&P.Mbf_hi[l], fmm::tc_bsplit_bytes(P.p, l, wide)) != cudaSuccess) ||
+        cudaMalloc(&P.Apre[l], fmm::tc_apre_bytes(P.p, wide)) != cudaSuccess)
       return FMM_ERR_ALLOC;
-    if (fmm::launch_tab_bf16(P, l, 0) != cudaSuccess || fmm::launch_build_a(P, l, 0) != cudaSuccess)
+    if ((!wide && fmm::launch_tab_bf16(P, l, 0) != cudaSuccess) || fmm::launch_build_a(P, l, 0) != cudaSuccess)
       return FMM_ERR_CUDA;
     const int rc = fmm::make_tc_map(P, l);
     if (rc != FMM_OK) return rc;
@@ -531,6 +533,7 @@ int fmm_plan_set_tc_min_level(fmm_plan* plan, int level) {
   if (!plan || level < fmm::kTcMinLevel || level > fmm::kMaxLevel + 1) return set_err(FMM_ERR_ARG);
   Plan& P = *reinterpret_cast<Plan*>(plan);
   P.tc_min_level = level;
+  P.tc_min_set = 1;
   if (P.tc_ready) {   // a lower first level needs its tiles now
     const int rc = prepare_tc(P);
     if (rc != FMM_OK) return set_err(rc);

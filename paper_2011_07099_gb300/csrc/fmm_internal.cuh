@@ -105,6 +105,7 @@ struct Plan {
   int m2l_fft = 0;                         // FFT form of the interaction zone at the fine levels (ablation)
   void* fft = nullptr;                     // its cuFFT plans and buffers (m2l_fft.cu)
   int tc_min_level = kTcMinLevel;          // first level on the tensor cores in the mixed forms
+  int tc_min_set = 0;                      // tc_min_level set by the caller (honoured at high order too)
   // near zone by FFT (p2p_fft.cu; 8-cell leaves): kernel spectra [72][27][4][32],
   // source spectra [72][leaves + 1][32] (last: all zero), target spectra [leaves][4][2304]
   int near_fft = 0;
@@ -156,10 +157,19 @@ inline bool wide_level(const Plan& P, int l) {
   return l <= kExtTopLevel || (P.p >= kWideOrder && l < P.L) || P.S >= kWideLeaf;
 }
 // First level of the tensor-core M2L in the mixed forms (above L: none; the
-// tensor-core kernel writes FP32 fields only, so 16-cell leaves do not use it).
+// tensor-core kernel writes FP32 fields, or the bf16x6 kernel FP64 ones, and
+// 16-cell leaves use neither).  At high order the wide levels from
+// kWideTcLevel down run the bf16x6 mode: measured on the 512^3 order-8
+// clustered workload, level 5 in bf16x6 costs 2.6e-6 / 5.8e-6 (Phi / g)
+// against the oracle, level 4 6.1e-5 (the coarser the level, the more its
+// far-field sums cancel), so the coarser wide levels keep the double-float
+// CUDA-core kernel.  A level set by the caller is taken as given.
+constexpr int kWideTcLevel = 5;
 inline int tc_first_level(const Plan& P) {
   if (P.S >= kWideLeaf) return P.L + 1;
-  return P.p >= kWideOrder ? (P.tc_min_level > P.L ? P.tc_min_level : P.L) : P.tc_min_level;
+  if (P.tc_min_set || P.p < kWideOrder) return P.tc_min_level;
+  const int wide_first = P.L < kWideTcLevel ? P.L : kWideTcLevel;
+  return P.tc_min_level > wide_first ? P.tc_min_level : wide_first;
 }
 
 cudaError_t setup_m2l_fp32(const Plan& P);
@@ -224,8 +234,12 @@ cudaError_t launch_grid_grad(Plan& P, float* grad, cudaStream_t s);
 cudaError_t launch_split_bf16(Plan& P, int level, cudaStream_t s);
 cudaError_t launch_m2l_tc(Plan& P, int level, int mode, cudaStream_t s);
 int tc_padded_k(int p);
-size_t tc_apre_bytes(int p);
-size_t tc_bsplit_bytes(int p, int level);
+// Tensor-core levels with FP64 local fields (the wide levels of high orders,
+// run only when the caller sets the first tensor-core level below the leaves)
+// use the bf16x6 mode: three-way splits and a double-float total.
+inline bool tc_wide(const Plan& P, int l) { return wide_level(P, l); }
+size_t tc_apre_bytes(int p, bool wide);
+size_t tc_bsplit_bytes(int p, int level, bool wide);
 // Encodes P.tmapB[level] for P.Mbf_hi[level] (FMM_* code).
 int make_tc_map(Plan& P, int level);
 cudaError_t launch_build_a(Plan& P, int level, cudaStream_t s);

@@ -40,6 +40,15 @@
 // tiles: 64-byte swizzle, K-major.  bf16x3 mode accumulates A_hi B_hi +
 // A_hi B_lo + A_lo B_hi; bf16 mode A_hi B_hi.
 // TMEM: 512 columns = partial (256) | total (256).
+// bf16x6 mode (the wide levels of high orders, whose local fields are FP64):
+// A from the double-float table and B from the FP64 masses, each split in
+// three BF16 parts; six products (hi hi, hi mid, mid hi, hi lo, mid mid,
+// lo hi); 128 targets per CTA (an 8 x 4 x 4 box of parents); every stage
+// accumulates into a fresh partial (two buffers, alternating), which the
+// drain adds into a double-float total by TwoSum; the level's FP64 local
+// field is written from hi + lo.  TMEM: partial 0 | partial 1 | hi | lo.
+// (A partial over a whole group of offsets cost 2.8e-5 at order 8: the
+// MMA's truncating accumulation, not the operand splits, dominated.)
 // Every wait is bounded; a timeout sets the plan's error word and later work
 // is skipped without leaving any barrier sequence.  Before the CTA exits the
 // issuer waits (bounded) for the completion of every MMA it issued and the
@@ -57,15 +66,26 @@ namespace fmm {
 namespace {
 
 constexpr int kKC = 32;          // reduction indices per pipeline stage
-constexpr int kNT = 256;         // targets per CTA (MMA N)
-constexpr int kBX = 8, kBY = 8, kBZ = 4;   // the targets' parents: an 8 x 8 x 4 box
+constexpr int kBX = 8, kBZ = 4;  // the targets' parents: an 8 x BY x 4 box
 constexpr int kHalo = 2;         // halo of the per-class source arrays (|(c - o - q)/2| <= 2)
 constexpr int kDrain = 128;      // drain threads (warps 2..5)
 constexpr int kThreads = 64 + kDrain;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kTileBytes = 128 * kKC * 2;     // one 128 x 32 BF16 tile of A
-constexpr int kTileB = kNT * kKC * 2;         // one 256 x 32 BF16 tile of B
-static_assert(kBX * kBY * kBZ == kNT, "target box");
+
+// Modes: 1 = BF16 (A_hi B_hi), 3 = bf16x3 (hi hi + hi lo + lo hi), 6 =
+// bf16x6: both operands split in three (hi, mid, lo), the six products down
+// to 2^-16 of hi hi, and the group partials added into a double-float total
+// (TMEM columns hi | lo) that is written as the level's FP64 local field —
+// the wide levels of high orders.
+template <int MODE>
+struct TcMode {
+  static constexpr int NSPLIT = MODE == 6 ? 3 : (MODE == 3 ? 2 : 1);   // splits of each operand used
+  static constexpr int ASPLIT = MODE == 6 ? 3 : 2;                     // A tiles stored per stage
+  static constexpr int NT = MODE == 6 ? 128 : 256;                     // targets per CTA (MMA N)
+  static constexpr int BY = NT / (kBX * kBZ);
+  static constexpr int TILEB = NT * kKC * 2;                           // one NT x 32 BF16 tile of B
+};
 
 template <int P, int MODE>
 struct TcShape {
@@ -73,8 +93,8 @@ struct TcShape {
   static constexpr int KP = ((P3 + kKC - 1) / kKC) * kKC;   // padded reduction length per offset
   static constexpr int NCH = KP / kKC;                       // stages per offset
   static constexpr int MT = (4 * P3 + 127) / 128;            // row tiles
-  static constexpr int NSPLIT = MODE == 3 ? 2 : 1;
-  static constexpr int STAGE_BYTES = NSPLIT * (kTileBytes + kTileB);
+  static constexpr int NSPLIT = TcMode<MODE>::NSPLIT;
+  static constexpr int STAGE_BYTES = NSPLIT * (kTileBytes + TcMode<MODE>::TILEB);
   static constexpr int EXTRA = 64;
   static constexpr int LIMIT = 225 * 1024;                  // dynamic shared memory budget
   static constexpr int FIT = (LIMIT - EXTRA - 1024) / STAGE_BYTES;
@@ -91,11 +111,14 @@ template <int P, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ Apre,
          const int8_t* __restrict__ offs, int n_off, int level, int group,
-         float* __restrict__ F, int* __restrict__ err, uint64_t kWaitNs, int stall) {
+         float* __restrict__ F, double* __restrict__ F64, int* __restrict__ err, uint64_t kWaitNs, int stall) {
   using Sh = TcShape<P, MODE>;
+  using Md = TcMode<MODE>;
   constexpr int P3 = Sh::P3, NCH = Sh::NCH, MT = Sh::MT, ST = Sh::ST, NSPLIT = Sh::NSPLIT;
   constexpr int STAGE_BYTES = Sh::STAGE_BYTES;
+  constexpr int kNT = Md::NT, kBY = Md::BY, kTileB = Md::TILEB, ASPLIT = Md::ASPLIT;
   static_assert(Sh::SMEM <= Sh::LIMIT, "shared-memory budget");
+  static_assert(kBX * kBY * kBZ == kNT, "target box");
   constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, kNT);
   constexpr uint32_t LBO_A = (128 / 8) * 128;      // next core matrix along K in an A tile
   constexpr uint32_t SBO_B = 8 * kKC * 2;          // 8 rows of 64 bytes in a B tile
@@ -103,9 +126,13 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
 
   extern __shared__ uint8_t smem[];
   // full: the stage's copies landed (A bulk + B tensor, counted in bytes);
-  // empty: the MMAs reading the stage are done; pfull / pfree: a group's
-  // partial is complete / has been added to the total.
-  __shared__ uint64_t full[ST], empty[ST], pfull, pfree, mdone;
+  // empty: the MMAs reading the stage are done; pfull / pfree: a unit's
+  // partial is complete / has been added to the total.  A unit is a group of
+  // `group` offsets (one partial buffer), or in bf16x6 one stage (two partial
+  // buffers, alternating): the truncating accumulation inside the MMA then
+  // spans only the stage's 12 products of 16 terms.
+  constexpr int NB = MODE == 6 ? 2 : 1;
+  __shared__ uint64_t full[ST], empty[ST], pfull[NB], pfree[NB], mdone;
   __shared__ uint32_t tmem_holder;
   __shared__ int s_err;
 
@@ -118,7 +145,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
   const int P0x = bx * kBX, P0y = by * kBY, P0z = bz * kBZ;     // the box of parents
   const int cx = ctype & 1, cy = (ctype >> 1) & 1, cz = ctype >> 2;
   const int8_t* my_offs = offs + (size_t)ctype * n_off * 3;
-  const int n_grp = (n_off + group - 1) / group;
+  const int n_units = MODE == 6 ? n_off * NCH : (n_off + group - 1) / group;
   // stages at a 1024-byte boundary (the swizzled B tiles need 512)
   const uint32_t smem_base = (tc::smem_u32(smem) + 1023u) & ~1023u;
 
@@ -128,8 +155,10 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
       tc::mbar_init(&full[i], 1);              // the expect_tx arrival (+ the stage's bytes)
       tc::mbar_init(&empty[i], 1);             // one MMA completion
     }
-    tc::mbar_init(&pfull, 1);
-    tc::mbar_init(&pfree, kDrain);
+    for (int b = 0; b < NB; ++b) {
+      tc::mbar_init(&pfull[b], 1);
+      tc::mbar_init(&pfree[b], kDrain);
+    }
     tc::mbar_init(&mdone, 1);
     tc::mbar_fence_init();
   }
@@ -138,7 +167,9 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_holder;
-  const uint32_t t_tot = tmem + kNT;
+  // TMEM columns: partial buffer(s) | total; bf16x6: partial 0 | partial 1 | total hi | total lo
+  const uint32_t t_tot = tmem + NB * kNT;
+  const uint32_t t_lo = tmem + (NB + 1) * kNT;
 
   if (warp == 0) {
     // ------------------------------------------------------------ MMA issuer
@@ -147,16 +178,16 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
     if (lane == 0) {
       bool ok = true;
       for (int io = 0; io < n_off && ok && !stall; ++io) {
-        const int g = io / group;
-        const bool first = (io % group) == 0;
-        // the partial is reused: the drain must have added group g - 1
-        if (first && g >= 1 && !tc::mbar_wait_bounded(&pfree, (uint32_t)(g - 1) & 1u, kWaitNs)) {
-          ok = false;
-          break;
-        }
-        tc::fence_after_sync();
         for (int ch = 0; ch < NCH; ++ch) {
           const int it = io * NCH + ch, st = it % ST;
+          const int u = MODE == 6 ? it : io / group;               // the unit this stage adds to
+          const bool first = MODE == 6 ? true : (io % group == 0 && ch == 0);
+          const uint32_t part = tmem + (uint32_t)((u % NB) * kNT);
+          // the partial buffer is reused: the drain must have added unit u - NB
+          if (first && u >= NB && !tc::mbar_wait_bounded(&pfree[u % NB], (uint32_t)(u / NB - 1) & 1u, kWaitNs)) {
+            ok = false;
+            break;
+          }
           if (!tc::mbar_wait_bounded(&full[st], (uint32_t)(it / ST) & 1u, kWaitNs)) {
             ok = false;
             break;
@@ -168,17 +199,25 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
           for (int j = 0; j < kKC / 16; ++j) {
             const uint64_t ah = tc::smem_desc(sA + j * 2 * LBO_A, LBO_A, 128);
             const uint64_t bh = tc::smem_desc_sw64(sB + j * 32, SBO_B);
-            tc::mma_bf16(tmem, ah, bh, IDESC, (!first || ch > 0 || j > 0) ? 1u : 0u);
-            if (MODE == 3) {
+            tc::mma_bf16(part, ah, bh, IDESC, (!first || j > 0) ? 1u : 0u);
+            if (MODE == 3 || MODE == 6) {
               const uint64_t al = tc::smem_desc(sA + kTileBytes + j * 2 * LBO_A, LBO_A, 128);
               const uint64_t bl = tc::smem_desc_sw64(sB + kTileB + j * 32, SBO_B);
-              tc::mma_bf16(tmem, ah, bl, IDESC, 1u);
-              tc::mma_bf16(tmem, al, bh, IDESC, 1u);
+              tc::mma_bf16(part, ah, bl, IDESC, 1u);
+              tc::mma_bf16(part, al, bh, IDESC, 1u);
+              if (MODE == 6) {       // al, bl are the mid splits here; a3, b3 the lo splits
+                const uint64_t a3 = tc::smem_desc(sA + 2 * kTileBytes + j * 2 * LBO_A, LBO_A, 128);
+                const uint64_t b3 = tc::smem_desc_sw64(sB + 2 * kTileB + j * 32, SBO_B);
+                tc::mma_bf16(part, ah, b3, IDESC, 1u);
+                tc::mma_bf16(part, al, bl, IDESC, 1u);
+                tc::mma_bf16(part, a3, bh, IDESC, 1u);
+              }
             }
           }
           tc::mma_commit(&empty[st]);
+          const bool last = MODE == 6 ? true : (ch == NCH - 1 && ((io % group) == group - 1 || io == n_off - 1));
+          if (last) tc::mma_commit(&pfull[u % NB]);
         }
-        if (ok && ((io % group) == group - 1 || io == n_off - 1)) tc::mma_commit(&pfull);
       }
       // every MMA this thread issued has finished before TMEM is released,
       // also when a wait gave up part-way
@@ -198,7 +237,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
         const int qx = (cx - ox) & 1, qy = (cy - oy) & 1, qz = (cz - oz) & 1;
         const int dx = (cx - ox - qx) / 2, dy = (cy - oy - qy) / 2, dz = (cz - oz - qz) / 2;
         const int q = qx | (qy << 1) | (qz << 2);
-        const uint8_t* atile = Apre + ((size_t)(off_index(ox, oy, oz) * MT + mt) * NCH) * 2 * kTileBytes;
+        const uint8_t* atile = Apre + ((size_t)(off_index(ox, oy, oz) * MT + mt) * NCH) * ASPLIT * kTileBytes;
         for (int ch = 0; ch < NCH; ++ch) {
           const int it = io * NCH + ch, st = it % ST;
           if (!tc::mbar_wait_bounded(&empty[st], ((uint32_t)(it / ST) & 1u) ^ 1u, kWaitNs)) {
@@ -208,8 +247,9 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
           const uint32_t sA = smem_base + st * STAGE_BYTES;
           const uint32_t sB = sA + NSPLIT * kTileBytes;
           tc::mbar_arrive_expect_tx(&full[st], TX);
-          tc::bulk_g2s(sA, atile + (size_t)ch * 2 * kTileBytes, kTileBytes, &full[st]);
-          if (MODE == 3) tc::bulk_g2s(sA + kTileBytes, atile + ((size_t)ch * 2 + 1) * kTileBytes, kTileBytes, &full[st]);
+          for (int sp = 0; sp < NSPLIT; ++sp)
+            tc::bulk_g2s(sA + sp * kTileBytes, atile + ((size_t)ch * ASPLIT + sp) * kTileBytes, kTileBytes,
+                         &full[st]);
           for (int sp = 0; sp < NSPLIT; ++sp)
             tc::tma_load_5d(sB + sp * kTileB, &tmapB, ch * kKC, P0x + dx + kHalo, P0y + dy + kHalo, P0z + dz + kHalo,
                             sp * 8 + q, &full[st]);
@@ -229,24 +269,42 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
     const int q = warp & 3;                          // TMEM lane quadrant
     const uint32_t lanebase = (uint32_t)(q * 32) << 16;
     bool ok = true;
-    for (int g = 0; g < n_grp; ++g) {
-      const bool got = ok && tc::mbar_wait_bounded(&pfull, (uint32_t)g & 1u, kWaitNs);
+    for (int g = 0; g < n_units; ++g) {
+      const bool got = ok && tc::mbar_wait_bounded(&pfull[g % NB], (uint32_t)(g / NB) & 1u, kWaitNs);
       ok = __all_sync(0xffffffffu, got);
       if (!ok) break;
       tc::fence_after_sync();
+      const uint32_t part = tmem + (uint32_t)((g % NB) * kNT);
       for (int c0 = 0; c0 < kNT; c0 += 32) {
-        uint32_t rp[32], rt[32];
-        tc::tmem_ld32_nowait(tmem + lanebase + c0, rp);
+        uint32_t rp[32], rt[32], rl[32];
+        tc::tmem_ld32_nowait(part + lanebase + c0, rp);
         if (g > 0) tc::tmem_ld32_nowait(t_tot + lanebase + c0, rt);
+        if (MODE == 6 && g > 0) tc::tmem_ld32_nowait(t_lo + lanebase + c0, rl);
         tc::tmem_wait_ld();
+        if (MODE == 6) {
+          // double-float total: (hi, lo) += partial by TwoSum, the error into lo
 #pragma unroll
-        for (int k = 0; k < 32; ++k)
-          rt[k] = g == 0 ? rp[k] : __float_as_uint(__uint_as_float(rt[k]) + __uint_as_float(rp[k]));
+          for (int k = 0; k < 32; ++k) {
+            if (g == 0) {
+              rt[k] = rp[k];
+              rl[k] = 0u;
+            } else {
+              const float2 t = df_two_sum(__uint_as_float(rt[k]), __uint_as_float(rp[k]));
+              rt[k] = __float_as_uint(t.x);
+              rl[k] = __float_as_uint(__fadd_rn(__uint_as_float(rl[k]), t.y));
+            }
+          }
+          tc::tmem_st32(t_lo + lanebase + c0, rl);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 32; ++k)
+            rt[k] = g == 0 ? rp[k] : __float_as_uint(__uint_as_float(rt[k]) + __uint_as_float(rp[k]));
+        }
         tc::tmem_st32(t_tot + lanebase + c0, rt);
       }
       tc::tmem_wait_st();
       tc::fence_before_sync();
-      tc::mbar_arrive(&pfree);
+      tc::mbar_arrive(&pfree[g % NB]);
     }
     // final: F = total.  Target t of the tile is the child of parent
     // P0 + (t % 8, (t / 8) % 8, t / 64) at the CTA's child position.
@@ -254,8 +312,9 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
       const int m = q * 32 + lane;
       const int gm = mt * 128 + m;
       for (int c0 = 0; c0 < kNT; c0 += 32) {
-        uint32_t rt[32];
+        uint32_t rt[32], rl[32];
         tc::tmem_ld32_nowait(t_tot + lanebase + c0, rt);
+        if (MODE == 6) tc::tmem_ld32_nowait(t_lo + lanebase + c0, rl);
         tc::tmem_wait_ld();
         if (gm < 4 * P3) {
 #pragma unroll
@@ -263,7 +322,11 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
             const int t = c0 + k;
             const uint32_t tx = 2u * (uint32_t)(P0x + t % kBX) + cx, ty = 2u * (uint32_t)(P0y + (t / kBX) % kBY) + cy,
                            tz = 2u * (uint32_t)(P0z + t / (kBX * kBY)) + cz;
-            F[(size_t)morton(tx, ty, tz) * 4 * P3 + gm] = __uint_as_float(rt[k]);
+            const size_t o = (size_t)morton(tx, ty, tz) * 4 * P3 + gm;
+            if (MODE == 6)
+              F64[o] = (double)__uint_as_float(rt[k]) + (double)__uint_as_float(rl[k]);
+            else
+              F[o] = __uint_as_float(rt[k]);
           }
         }
       }
@@ -340,12 +403,12 @@ cudaError_t launch_one(Plan& Pl, int level, cudaStream_t s) {
   const int nh = 1 << (level - 1);
   // target boxes fastest: the CTAs in flight share row tile and child type,
   // hence their A tiles, which L2 then serves to all of them
-  dim3 grid((nh / kBX) * (nh / kBY) * (nh / kBZ), TcShape<P, MODE>::MT, 8);
+  dim3 grid((nh / kBX) * (nh / TcMode<MODE>::BY) * (nh / kBZ), TcShape<P, MODE>::MT, 8);
   const CUtensorMap* map = static_cast<const CUtensorMap*>(Pl.tmapB[level]);
   const uint8_t* Apre = static_cast<const uint8_t*>(Pl.Apre[level]);
   k_m2l_tc<P, MODE><<<grid, kThreads, smem_bytes<P, MODE>(), s>>>(
-      *map, Apre, Pl.offsets[level], Pl.n_off[level], level, Pl.tc_group, Pl.F[level], Pl.d_err, Pl.wait_ns,
-      Pl.inject_stall);
+      *map, Apre, Pl.offsets[level], Pl.n_off[level], level, Pl.tc_group, Pl.F[level], Pl.F64[level], Pl.d_err,
+      Pl.wait_ns, Pl.inject_stall);
   return cudaGetLastError();
 }
 
@@ -353,18 +416,75 @@ template <int P>
 cudaError_t setup_p() {
   cudaError_t e;
   if ((e = setup_one<P, 1>()) != cudaSuccess) return e;
+  if (P >= kWideOrder && (e = setup_one<(P >= kWideOrder ? P : kWideOrder), 6>()) != cudaSuccess) return e;
   return setup_one<P, 3>();
 }
 
 template <int P>
 cudaError_t launch_p(Plan& Pl, int level, int mode, cudaStream_t s) {
+  if (tc_wide(Pl, level)) {
+    if (P < kWideOrder) return cudaErrorInvalidValue;
+    return launch_one<(P >= kWideOrder ? P : kWideOrder), 6>(Pl, level, s);
+  }
   if (mode == FMM_PREC_BF16X3) return launch_one<P, 3>(Pl, level, s);
   return launch_one<P, 1>(Pl, level, s);
 }
 
+// Plan time, bf16x6 levels: the translation tiles split in three from the
+// double-float table entries (G = tab + tab_lo, the wide levels keep both),
+// hi = bf16(v), mid = bf16(v - hi), lo = bf16(v - hi - mid) (the differences
+// in FP64), in the layout of k_build_a, three tiles per stage.
+template <int P>
+__global__ void k_build_a3(const float4* __restrict__ tab, const float4* __restrict__ tab_lo,
+                           uint8_t* __restrict__ out) {
+  constexpr int P3 = P * P * P, KP = ((P3 + kKC - 1) / kKC) * kKC, NCH = KP / kKC, MT = (4 * P3 + 127) / 128;
+  constexpr int HW = 4 * P - 1, E = 8 * P - 1;
+  const size_t rows = (size_t)kOffSlots * MT * NCH * 512;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < rows; i += (size_t)gridDim.x * blockDim.x) {
+    const int rowin = (int)(i % 512);
+    const size_t tile = i / 512;
+    const int ch = (int)(tile % NCH);
+    const int mt = (int)((tile / NCH) % MT);
+    const int oi = (int)(tile / ((size_t)NCH * MT));
+    const int ox = oi % 7 - 3, oy = (oi / 7) % 7 - 3, oz = oi / 49 - 3;
+    const int m = rowin % 128, kc8 = rowin / 128;
+    const int gm = mt * 128 + m;
+    uint32_t w[3][4] = {};
+    const bool far = ox < -1 || ox > 1 || oy < -1 || oy > 1 || oz < -1 || oz > 1;
+    if (far && gm < 4 * P3) {
+      const int f = gm / P3, r = gm % P3;
+      const int rx = r % P, ry = (r / P) % P, rz = r / (P * P);
+      for (int e = 0; e < 8; ++e) {
+        const int s = ch * kKC + kc8 * 8 + e;
+        double v = 0.0;
+        if (s < P3) {
+          const int sx = s % P, sy = (s / P) % P, sz = s / (P * P);
+          const int nx = ox * P + rx - sx + HW, ny = oy * P + ry - sy + HW, nz = oz * P + rz - sz + HW;
+          const size_t t = ((size_t)nz * E + ny) * E + nx;
+          const float4 a = tab[t], b = tab_lo[t];
+          v = (double)(f == 0 ? a.x : (f == 1 ? a.y : (f == 2 ? a.z : a.w))) +
+              (double)(f == 0 ? b.x : (f == 1 ? b.y : (f == 2 ? b.z : b.w)));
+        }
+        for (int sp = 0; sp < 3; ++sp) {
+          const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+          v -= (double)__bfloat162float(h);
+          const uint32_t bits = (uint32_t)__bfloat16_as_ushort(h);
+          w[sp][e / 2] |= (e & 1) ? bits << 16 : bits;
+        }
+      }
+    }
+    const size_t base = tile * 3 * kTileBytes + (size_t)((kc8 * 16 + m / 8) * 128 + (m % 8) * 16);
+    for (int sp = 0; sp < 3; ++sp)
+      *reinterpret_cast<uint4*>(out + base + sp * kTileBytes) = make_uint4(w[sp][0], w[sp][1], w[sp][2], w[sp][3]);
+  }
+}
+
 template <int P>
 cudaError_t build_a_p(Plan& Pl, int level, cudaStream_t s) {
-  k_build_a<P><<<8 * Pl.num_sms, 256, 0, s>>>(Pl.tab_bf[level], static_cast<uint8_t*>(Pl.Apre[level]));
+  if (tc_wide(Pl, level))
+    k_build_a3<P><<<8 * Pl.num_sms, 256, 0, s>>>(Pl.tab[level], Pl.tab_lo[level], static_cast<uint8_t*>(Pl.Apre[level]));
+  else
+    k_build_a<P><<<8 * Pl.num_sms, 256, 0, s>>>(Pl.tab_bf[level], static_cast<uint8_t*>(Pl.Apre[level]));
   return cudaGetLastError();
 }
 
@@ -373,8 +493,8 @@ cudaError_t build_a_p(Plan& Pl, int level, cudaStream_t s) {
 // parity class ((x & 1) | (y & 1) << 1 | (z & 1) << 2) and (x, y, z) its
 // coordinates within the class (halved); the halo holds the periodic copies,
 // or zeros for the isolated problem; rows padded to KP with zeros.
-__global__ void k_split_bf16(const float* __restrict__ M, int p3, int kp, int level, int iso,
-                             __nv_bfloat16* __restrict__ out) {
+__global__ void k_split_bf16(const float* __restrict__ M, const double* __restrict__ M64, int p3, int kp, int level,
+                             int iso, __nv_bfloat16* __restrict__ out) {
   const int nh = 1 << (level - 1), W = nh + 2 * kHalo;
   const size_t row = (size_t)kp, cls = (size_t)W * W * W * row, total = 8 * cls;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
@@ -384,35 +504,40 @@ __global__ void k_split_bf16(const float* __restrict__ M, int p3, int kp, int le
     const int q = (int)(cell / ((size_t)W * W * W));
     int ux = xw - kHalo, uy = yw - kHalo, uz = zw - kHalo;
     const bool inbox = (unsigned)ux < (unsigned)nh && (unsigned)uy < (unsigned)nh && (unsigned)uz < (unsigned)nh;
-    float x = 0.f;
+    double x = 0.0;
     if (k < p3 && (inbox || !iso)) {
       ux = (ux + nh) % nh;
       uy = (uy + nh) % nh;
       uz = (uz + nh) % nh;
       const uint32_t key = morton(2u * ux + (q & 1), 2u * uy + ((q >> 1) & 1), 2u * uz + (q >> 2));
-      x = M[(size_t)key * p3 + k];
+      x = M64 ? M64[(size_t)key * p3 + k] : (double)M[(size_t)key * p3 + k];
     }
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    out[i] = h;
-    out[total + i] = __float2bfloat16_rn(x - __bfloat162float(h));
+    // two splits (hi, lo) from FP32 masses, or three (hi, mid, lo) from the
+    // FP64 masses of a bf16x6 level
+    for (int sp = 0; sp < (M64 ? 3 : 2); ++sp) {
+      const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
+      out[sp * total + i] = h;
+      x -= (double)__bfloat162float(h);
+    }
   }
 }
 
 }  // namespace
 
-size_t tc_apre_bytes(int p) {
+size_t tc_apre_bytes(int p, bool wide) {
   const int p3 = p * p * p;
   const int kp = ((p3 + kKC - 1) / kKC) * kKC, nch = kp / kKC, mt = (4 * p3 + 127) / 128;
-  return (size_t)kOffSlots * mt * nch * 2 * kTileBytes;
+  return (size_t)kOffSlots * mt * nch * (wide ? 3 : 2) * kTileBytes;
 }
 
-size_t tc_bsplit_bytes(int p, int level) {
+size_t tc_bsplit_bytes(int p, int level, bool wide) {
   const size_t W = (size_t)(1 << (level - 1)) + 2 * kHalo;
-  return 2 * 8 * W * W * W * (size_t)tc_padded_k(p) * sizeof(__nv_bfloat16);
+  return (wide ? 3 : 2) * 8 * W * W * W * (size_t)tc_padded_k(p) * sizeof(__nv_bfloat16);
 }
 
 // The 5-D tensor map of a level's split multipoles: dims (KP, W, W, W,
-// 16 = split x class), box (32, 8, 8, 4, 1), 64-byte swizzle.
+// 8 x splits = split x class), box (32, 8, BY, 4, 1) (BY = 8, or 4 for the
+// 128-target tiles of bf16x6), 64-byte swizzle.
 int make_tc_map(Plan& P, int level) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -426,9 +551,11 @@ int make_tc_map(Plan& P, int level) {
   if (!P.tmapB[level]) P.tmapB[level] = new (std::nothrow) CUtensorMap;
   if (!P.tmapB[level]) return FMM_ERR_ALLOC;
   const cuuint64_t kp = (cuuint64_t)tc_padded_k(P.p), W = (cuuint64_t)(1 << (level - 1)) + 2 * kHalo;
-  const cuuint64_t dims[5] = {kp, W, W, W, 16};
+  const bool wide = tc_wide(P, level);
+  const cuuint64_t dims[5] = {kp, W, W, W, (cuuint64_t)(wide ? 24 : 16)};
   const cuuint64_t strides[4] = {kp * 2, kp * 2 * W, kp * 2 * W * W, kp * 2 * W * W * W};
-  const cuuint32_t box[5] = {(cuuint32_t)kKC, (cuuint32_t)kBX, (cuuint32_t)kBY, (cuuint32_t)kBZ, 1};
+  const cuuint32_t box[5] = {(cuuint32_t)kKC, (cuuint32_t)kBX, (cuuint32_t)(wide ? TcMode<6>::BY : TcMode<3>::BY),
+                             (cuuint32_t)kBZ, 1};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   const CUresult r = encode(static_cast<CUtensorMap*>(P.tmapB[level]), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5,
                             P.Mbf_hi[level], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -470,7 +597,8 @@ cudaError_t setup_m2l_tc(const Plan& P) {
 
 cudaError_t launch_split_bf16(Plan& P, int level, cudaStream_t s) {
   const int p3 = P.p * P.p * P.p;
-  k_split_bf16<<<8 * P.num_sms, 256, 0, s>>>(P.M[level], p3, tc_padded_k(P.p), level, P.iso,
+  k_split_bf16<<<8 * P.num_sms, 256, 0, s>>>(P.M[level], tc_wide(P, level) ? P.M64[level] : nullptr, p3,
+                                            tc_padded_k(P.p), level, P.iso,
                                             static_cast<__nv_bfloat16*>(P.Mbf_hi[level]));
   return cudaGetLastError();
 }
