@@ -372,10 +372,10 @@ int prepare_tc(Plan& P) {
   bool made = false;
   for (int l = fmm::tc_first_level(P); l <= P.L; ++l) {
     if (P.Apre[l]) continue;
-    const bool wide = fmm::tc_wide(P, l);   // bf16x6: tiles from tab + tab_lo, no BF16 table
+    const bool wide = fmm::tc_wide(P, l);   // wide modes: tiles from tab + tab_lo, no BF16 table
     if ((!wide && !P.tab_bf[l] && !dev_alloc(&P.tab_bf[l], E * E * E)) ||
-        (!P.Mbf_hi[l] && cudaMalloc(&P.Mbf_hi[l], fmm::tc_bsplit_bytes(P.p, l, wide)) != cudaSuccess) ||
-        cudaMalloc(&P.Apre[l], fmm::tc_apre_bytes(P.p, wide)) != cudaSuccess)
+        (!P.Mbf_hi[l] && cudaMalloc(&P.Mbf_hi[l], fmm::tc_bsplit_bytes(P.p, l, fmm::tc_splits(P, l))) != cudaSuccess) ||
+        cudaMalloc(&P.Apre[l], fmm::tc_apre_bytes(P.p, fmm::tc_splits(P, l))) != cudaSuccess)
       return FMM_ERR_ALLOC;
     if ((!wide && fmm::launch_tab_bf16(P, l, 0) != cudaSuccess) || fmm::launch_build_a(P, l, 0) != cudaSuccess)
       return FMM_ERR_CUDA;

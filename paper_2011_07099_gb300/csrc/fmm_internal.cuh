@@ -234,12 +234,13 @@ cudaError_t launch_grid_grad(Plan& P, float* grad, cudaStream_t s);
 cudaError_t launch_split_bf16(Plan& P, int level, cudaStream_t s);
 cudaError_t launch_m2l_tc(Plan& P, int level, int mode, cudaStream_t s);
 int tc_padded_k(int p);
-// Tensor-core levels with FP64 local fields (the wide levels of high orders,
-// run only when the caller sets the first tensor-core level below the leaves)
-// use the bf16x6 mode: three-way splits and a double-float total.
+// Tensor-core levels with FP64 local fields (the wide levels of high orders)
+// use the bf16x6 mode: operands split in three BF16 parts, partials added
+// into a double-float total.
 inline bool tc_wide(const Plan& P, int l) { return wide_level(P, l); }
-size_t tc_apre_bytes(int p, bool wide);
-size_t tc_bsplit_bytes(int p, int level, bool wide);
+inline int tc_splits(const Plan& P, int l) { return tc_wide(P, l) ? 3 : 2; }
+size_t tc_apre_bytes(int p, int nsplit);
+size_t tc_bsplit_bytes(int p, int level, int nsplit);
 // Encodes P.tmapB[level] for P.Mbf_hi[level] (FMM_* code).
 int make_tc_map(Plan& P, int level);
 cudaError_t launch_build_a(Plan& P, int level, cudaStream_t s);

@@ -68,23 +68,30 @@ namespace {
 constexpr int kKC = 32;          // reduction indices per pipeline stage
 constexpr int kBX = 8, kBZ = 4;  // the targets' parents: an 8 x BY x 4 box
 constexpr int kHalo = 2;         // halo of the per-class source arrays (|(c - o - q)/2| <= 2)
-constexpr int kDrain = 128;      // drain threads (warps 2..5)
-constexpr int kThreads = 64 + kDrain;
+constexpr int kDrainMax = 256;   // drain threads: warps 2..5 (2..9 in bf16x6)
 constexpr uint32_t kTmemCols = 512;
 constexpr int kTileBytes = 128 * kKC * 2;     // one 128 x 32 BF16 tile of A
 
-// Modes: 1 = BF16 (A_hi B_hi), 3 = bf16x3 (hi hi + hi lo + lo hi), 6 =
-// bf16x6: both operands split in three (hi, mid, lo), the six products down
-// to 2^-16 of hi hi, and the group partials added into a double-float total
-// (TMEM columns hi | lo) that is written as the level's FP64 local field —
-// the wide levels of high orders.
+// Modes: 1 = BF16 (A_hi B_hi), 3 = bf16x3 (hi hi + hi lo + lo hi); the
+// wide mode of the FP64-field levels of high orders: 6 = bf16x6, both
+// operands split in three BF16 parts and the six products s_i t_j with
+// i + j <= 2, each stage's partial added into a double-float total (TMEM
+// columns hi | lo) that is written as the level's FP64 local field.  (Four
+// parts and ten products measured the same error at order 8, level 4: there
+// the truncating accumulation inside each stage's MMAs, not the operands,
+// limits; that level stays on the double-float CUDA-core kernel.)
 template <int MODE>
 struct TcMode {
+  static constexpr bool WIDE = MODE >= 6;
   static constexpr int NSPLIT = MODE == 6 ? 3 : (MODE == 3 ? 2 : 1);   // splits of each operand used
-  static constexpr int ASPLIT = MODE == 6 ? 3 : 2;                     // A tiles stored per stage
-  static constexpr int NT = MODE == 6 ? 128 : 256;                     // targets per CTA (MMA N)
+  static constexpr int ASPLIT = WIDE ? NSPLIT : 2;                     // A tiles stored per stage
+  static constexpr int NT = WIDE ? 128 : 256;                          // targets per CTA (MMA N)
   static constexpr int BY = NT / (kBX * kBZ);
   static constexpr int TILEB = NT * kKC * 2;                           // one NT x 32 BF16 tile of B
+  // drain threads: bf16x6 adds a partial per stage into a double-float total,
+  // so two warps share each TMEM lane quadrant, one half of the columns each
+  static constexpr int DRAIN = WIDE ? 256 : 128;
+  static constexpr int THREADS = 64 + DRAIN;
 };
 
 template <int P, int MODE>
@@ -108,7 +115,7 @@ __host__ __device__ constexpr int off_index(int ox, int oy, int oz) { return ((o
 constexpr int kOffSlots = 343;
 
 template <int P, int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(64 + kDrainMax, 1)
 k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ Apre,
          const int8_t* __restrict__ offs, int n_off, int level, int group,
          float* __restrict__ F, double* __restrict__ F64, int* __restrict__ err, uint64_t kWaitNs, int stall) {
@@ -131,7 +138,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
   // `group` offsets (one partial buffer), or in bf16x6 one stage (two partial
   // buffers, alternating): the truncating accumulation inside the MMA then
   // spans only the stage's 12 products of 16 terms.
-  constexpr int NB = MODE == 6 ? 2 : 1;
+  constexpr int NB = Md::WIDE ? 2 : 1;
   __shared__ uint64_t full[ST], empty[ST], pfull[NB], pfree[NB], mdone;
   __shared__ uint32_t tmem_holder;
   __shared__ int s_err;
@@ -145,7 +152,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
   const int P0x = bx * kBX, P0y = by * kBY, P0z = bz * kBZ;     // the box of parents
   const int cx = ctype & 1, cy = (ctype >> 1) & 1, cz = ctype >> 2;
   const int8_t* my_offs = offs + (size_t)ctype * n_off * 3;
-  const int n_units = MODE == 6 ? n_off * NCH : (n_off + group - 1) / group;
+  const int n_units = Md::WIDE ? n_off * NCH : (n_off + group - 1) / group;
   // stages at a 1024-byte boundary (the swizzled B tiles need 512)
   const uint32_t smem_base = (tc::smem_u32(smem) + 1023u) & ~1023u;
 
@@ -157,7 +164,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
     }
     for (int b = 0; b < NB; ++b) {
       tc::mbar_init(&pfull[b], 1);
-      tc::mbar_init(&pfree[b], kDrain);
+      tc::mbar_init(&pfree[b], Md::DRAIN);
     }
     tc::mbar_init(&mdone, 1);
     tc::mbar_fence_init();
@@ -180,8 +187,8 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
       for (int io = 0; io < n_off && ok && !stall; ++io) {
         for (int ch = 0; ch < NCH; ++ch) {
           const int it = io * NCH + ch, st = it % ST;
-          const int u = MODE == 6 ? it : io / group;               // the unit this stage adds to
-          const bool first = MODE == 6 ? true : (io % group == 0 && ch == 0);
+          const int u = Md::WIDE ? it : io / group;                // the unit this stage adds to
+          const bool first = Md::WIDE ? true : (io % group == 0 && ch == 0);
           const uint32_t part = tmem + (uint32_t)((u % NB) * kNT);
           // the partial buffer is reused: the drain must have added unit u - NB
           if (first && u >= NB && !tc::mbar_wait_bounded(&pfree[u % NB], (uint32_t)(u / NB - 1) & 1u, kWaitNs)) {
@@ -197,25 +204,30 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
           const uint32_t sB = sA + NSPLIT * kTileBytes;
 #pragma unroll
           for (int j = 0; j < kKC / 16; ++j) {
-            const uint64_t ah = tc::smem_desc(sA + j * 2 * LBO_A, LBO_A, 128);
-            const uint64_t bh = tc::smem_desc_sw64(sB + j * 32, SBO_B);
-            tc::mma_bf16(part, ah, bh, IDESC, (!first || j > 0) ? 1u : 0u);
-            if (MODE == 3 || MODE == 6) {
-              const uint64_t al = tc::smem_desc(sA + kTileBytes + j * 2 * LBO_A, LBO_A, 128);
-              const uint64_t bl = tc::smem_desc_sw64(sB + kTileB + j * 32, SBO_B);
-              tc::mma_bf16(part, ah, bl, IDESC, 1u);
-              tc::mma_bf16(part, al, bh, IDESC, 1u);
-              if (MODE == 6) {       // al, bl are the mid splits here; a3, b3 the lo splits
-                const uint64_t a3 = tc::smem_desc(sA + 2 * kTileBytes + j * 2 * LBO_A, LBO_A, 128);
-                const uint64_t b3 = tc::smem_desc_sw64(sB + 2 * kTileB + j * 32, SBO_B);
-                tc::mma_bf16(part, ah, b3, IDESC, 1u);
-                tc::mma_bf16(part, al, bl, IDESC, 1u);
-                tc::mma_bf16(part, a3, bh, IDESC, 1u);
+            if constexpr (Md::WIDE) {
+              // the products s_a t_b with a + b < NSPLIT, largest first
+#pragma unroll
+              for (int d = 0; d < NSPLIT; ++d)
+#pragma unroll
+                for (int a = 0; a <= d; ++a) {
+                  const uint64_t ad = tc::smem_desc(sA + a * kTileBytes + j * 2 * LBO_A, LBO_A, 128);
+                  const uint64_t bd = tc::smem_desc_sw64(sB + (d - a) * kTileB + j * 32, SBO_B);
+                  tc::mma_bf16(part, ad, bd, IDESC, (d == 0 && j == 0) ? 0u : 1u);
+                }
+            } else {
+              const uint64_t ah = tc::smem_desc(sA + j * 2 * LBO_A, LBO_A, 128);
+              const uint64_t bh = tc::smem_desc_sw64(sB + j * 32, SBO_B);
+              tc::mma_bf16(part, ah, bh, IDESC, (!first || j > 0) ? 1u : 0u);
+              if (MODE == 3) {
+                const uint64_t al = tc::smem_desc(sA + kTileBytes + j * 2 * LBO_A, LBO_A, 128);
+                const uint64_t bl = tc::smem_desc_sw64(sB + kTileB + j * 32, SBO_B);
+                tc::mma_bf16(part, ah, bl, IDESC, 1u);
+                tc::mma_bf16(part, al, bh, IDESC, 1u);
               }
             }
           }
           tc::mma_commit(&empty[st]);
-          const bool last = MODE == 6 ? true : (ch == NCH - 1 && ((io % group) == group - 1 || io == n_off - 1));
+          const bool last = Md::WIDE ? true : (ch == NCH - 1 && ((io % group) == group - 1 || io == n_off - 1));
           if (last) tc::mma_commit(&pfull[u % NB]);
         }
       }
@@ -268,6 +280,9 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
     // ------------------------------------------------------------ drain warps
     const int q = warp & 3;                          // TMEM lane quadrant
     const uint32_t lanebase = (uint32_t)(q * 32) << 16;
+    // columns of this warp: all, or (bf16x6) one half
+    constexpr int CW = kNT * 128 / Md::DRAIN;
+    const int cbeg = ((warp - 2) / 4) * CW, cend = cbeg + CW;
     bool ok = true;
     for (int g = 0; g < n_units; ++g) {
       const bool got = ok && tc::mbar_wait_bounded(&pfull[g % NB], (uint32_t)(g / NB) & 1u, kWaitNs);
@@ -275,13 +290,13 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
       if (!ok) break;
       tc::fence_after_sync();
       const uint32_t part = tmem + (uint32_t)((g % NB) * kNT);
-      for (int c0 = 0; c0 < kNT; c0 += 32) {
+      for (int c0 = cbeg; c0 < cend; c0 += 32) {
         uint32_t rp[32], rt[32], rl[32];
         tc::tmem_ld32_nowait(part + lanebase + c0, rp);
         if (g > 0) tc::tmem_ld32_nowait(t_tot + lanebase + c0, rt);
-        if (MODE == 6 && g > 0) tc::tmem_ld32_nowait(t_lo + lanebase + c0, rl);
+        if (Md::WIDE && g > 0) tc::tmem_ld32_nowait(t_lo + lanebase + c0, rl);
         tc::tmem_wait_ld();
-        if (MODE == 6) {
+        if (Md::WIDE) {
           // double-float total: (hi, lo) += partial by TwoSum, the error into lo
 #pragma unroll
           for (int k = 0; k < 32; ++k) {
@@ -311,10 +326,10 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
     if (ok && n_off > 0 && __all_sync(0xffffffffu, atomicAdd(&s_err, 0) == 0)) {
       const int m = q * 32 + lane;
       const int gm = mt * 128 + m;
-      for (int c0 = 0; c0 < kNT; c0 += 32) {
+      for (int c0 = cbeg; c0 < cend; c0 += 32) {
         uint32_t rt[32], rl[32];
         tc::tmem_ld32_nowait(t_tot + lanebase + c0, rt);
-        if (MODE == 6) tc::tmem_ld32_nowait(t_lo + lanebase + c0, rl);
+        if (Md::WIDE) tc::tmem_ld32_nowait(t_lo + lanebase + c0, rl);
         tc::tmem_wait_ld();
         if (gm < 4 * P3) {
 #pragma unroll
@@ -323,7 +338,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ 
             const uint32_t tx = 2u * (uint32_t)(P0x + t % kBX) + cx, ty = 2u * (uint32_t)(P0y + (t / kBX) % kBY) + cy,
                            tz = 2u * (uint32_t)(P0z + t / (kBX * kBY)) + cz;
             const size_t o = (size_t)morton(tx, ty, tz) * 4 * P3 + gm;
-            if (MODE == 6)
+            if (Md::WIDE)
               F64[o] = (double)__uint_as_float(rt[k]) + (double)__uint_as_float(rl[k]);
             else
               F[o] = __uint_as_float(rt[k]);
@@ -406,7 +421,7 @@ cudaError_t launch_one(Plan& Pl, int level, cudaStream_t s) {
   dim3 grid((nh / kBX) * (nh / TcMode<MODE>::BY) * (nh / kBZ), TcShape<P, MODE>::MT, 8);
   const CUtensorMap* map = static_cast<const CUtensorMap*>(Pl.tmapB[level]);
   const uint8_t* Apre = static_cast<const uint8_t*>(Pl.Apre[level]);
-  k_m2l_tc<P, MODE><<<grid, kThreads, smem_bytes<P, MODE>(), s>>>(
+  k_m2l_tc<P, MODE><<<grid, TcMode<MODE>::THREADS, smem_bytes<P, MODE>(), s>>>(
       *map, Apre, Pl.offsets[level], Pl.n_off[level], level, Pl.tc_group, Pl.F[level], Pl.F64[level], Pl.d_err,
       Pl.wait_ns, Pl.inject_stall);
   return cudaGetLastError();
@@ -416,26 +431,28 @@ template <int P>
 cudaError_t setup_p() {
   cudaError_t e;
   if ((e = setup_one<P, 1>()) != cudaSuccess) return e;
-  if (P >= kWideOrder && (e = setup_one<(P >= kWideOrder ? P : kWideOrder), 6>()) != cudaSuccess) return e;
+  constexpr int PW = P >= kWideOrder ? P : kWideOrder;   // the wide modes exist at high orders only
+  if (P >= kWideOrder && (e = setup_one<PW, 6>()) != cudaSuccess) return e;
   return setup_one<P, 3>();
 }
 
 template <int P>
 cudaError_t launch_p(Plan& Pl, int level, int mode, cudaStream_t s) {
   if (tc_wide(Pl, level)) {
+    constexpr int PW = P >= kWideOrder ? P : kWideOrder;
     if (P < kWideOrder) return cudaErrorInvalidValue;
-    return launch_one<(P >= kWideOrder ? P : kWideOrder), 6>(Pl, level, s);
+    return launch_one<PW, 6>(Pl, level, s);
   }
   if (mode == FMM_PREC_BF16X3) return launch_one<P, 3>(Pl, level, s);
   return launch_one<P, 1>(Pl, level, s);
 }
 
-// Plan time, bf16x6 levels: the translation tiles split in three from the
-// double-float table entries (G = tab + tab_lo, the wide levels keep both),
-// hi = bf16(v), mid = bf16(v - hi), lo = bf16(v - hi - mid) (the differences
-// in FP64), in the layout of k_build_a, three tiles per stage.
-template <int P>
-__global__ void k_build_a3(const float4* __restrict__ tab, const float4* __restrict__ tab_lo,
+// Plan time, wide levels: the translation tiles split in NS BF16 parts from
+// the double-float table entries (G = tab + tab_lo, the wide levels keep
+// both): s_0 = bf16(v), s_1 = bf16(v - s_0), ... (the differences in FP64),
+// in the layout of k_build_a, NS tiles per stage.
+template <int P, int NS>
+__global__ void k_build_aw(const float4* __restrict__ tab, const float4* __restrict__ tab_lo,
                            uint8_t* __restrict__ out) {
   constexpr int P3 = P * P * P, KP = ((P3 + kKC - 1) / kKC) * kKC, NCH = KP / kKC, MT = (4 * P3 + 127) / 128;
   constexpr int HW = 4 * P - 1, E = 8 * P - 1;
@@ -449,7 +466,7 @@ __global__ void k_build_a3(const float4* __restrict__ tab, const float4* __restr
     const int ox = oi % 7 - 3, oy = (oi / 7) % 7 - 3, oz = oi / 49 - 3;
     const int m = rowin % 128, kc8 = rowin / 128;
     const int gm = mt * 128 + m;
-    uint32_t w[3][4] = {};
+    uint32_t w[NS][4] = {};
     const bool far = ox < -1 || ox > 1 || oy < -1 || oy > 1 || oz < -1 || oz > 1;
     if (far && gm < 4 * P3) {
       const int f = gm / P3, r = gm % P3;
@@ -465,7 +482,7 @@ __global__ void k_build_a3(const float4* __restrict__ tab, const float4* __restr
           v = (double)(f == 0 ? a.x : (f == 1 ? a.y : (f == 2 ? a.z : a.w))) +
               (double)(f == 0 ? b.x : (f == 1 ? b.y : (f == 2 ? b.z : b.w)));
         }
-        for (int sp = 0; sp < 3; ++sp) {
+        for (int sp = 0; sp < NS; ++sp) {
           const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
           v -= (double)__bfloat162float(h);
           const uint32_t bits = (uint32_t)__bfloat16_as_ushort(h);
@@ -473,8 +490,8 @@ __global__ void k_build_a3(const float4* __restrict__ tab, const float4* __restr
         }
       }
     }
-    const size_t base = tile * 3 * kTileBytes + (size_t)((kc8 * 16 + m / 8) * 128 + (m % 8) * 16);
-    for (int sp = 0; sp < 3; ++sp)
+    const size_t base = tile * NS * kTileBytes + (size_t)((kc8 * 16 + m / 8) * 128 + (m % 8) * 16);
+    for (int sp = 0; sp < NS; ++sp)
       *reinterpret_cast<uint4*>(out + base + sp * kTileBytes) = make_uint4(w[sp][0], w[sp][1], w[sp][2], w[sp][3]);
   }
 }
@@ -482,7 +499,7 @@ __global__ void k_build_a3(const float4* __restrict__ tab, const float4* __restr
 template <int P>
 cudaError_t build_a_p(Plan& Pl, int level, cudaStream_t s) {
   if (tc_wide(Pl, level))
-    k_build_a3<P><<<8 * Pl.num_sms, 256, 0, s>>>(Pl.tab[level], Pl.tab_lo[level], static_cast<uint8_t*>(Pl.Apre[level]));
+    k_build_aw<P, 3><<<8 * Pl.num_sms, 256, 0, s>>>(Pl.tab[level], Pl.tab_lo[level], static_cast<uint8_t*>(Pl.Apre[level]));
   else
     k_build_a<P><<<8 * Pl.num_sms, 256, 0, s>>>(Pl.tab_bf[level], static_cast<uint8_t*>(Pl.Apre[level]));
   return cudaGetLastError();
@@ -493,8 +510,8 @@ cudaError_t build_a_p(Plan& Pl, int level, cudaStream_t s) {
 // parity class ((x & 1) | (y & 1) << 1 | (z & 1) << 2) and (x, y, z) its
 // coordinates within the class (halved); the halo holds the periodic copies,
 // or zeros for the isolated problem; rows padded to KP with zeros.
-__global__ void k_split_bf16(const float* __restrict__ M, const double* __restrict__ M64, int p3, int kp, int level,
-                             int iso, __nv_bfloat16* __restrict__ out) {
+__global__ void k_split_bf16(const float* __restrict__ M, const double* __restrict__ M64, int nsplit, int p3, int kp,
+                             int level, int iso, __nv_bfloat16* __restrict__ out) {
   const int nh = 1 << (level - 1), W = nh + 2 * kHalo;
   const size_t row = (size_t)kp, cls = (size_t)W * W * W * row, total = 8 * cls;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
@@ -513,8 +530,8 @@ __global__ void k_split_bf16(const float* __restrict__ M, const double* __restri
       x = M64 ? M64[(size_t)key * p3 + k] : (double)M[(size_t)key * p3 + k];
     }
     // two splits (hi, lo) from FP32 masses, or three (hi, mid, lo) from the
-    // FP64 masses of a bf16x6 level
-    for (int sp = 0; sp < (M64 ? 3 : 2); ++sp) {
+    // FP64 masses of a wide level
+    for (int sp = 0; sp < nsplit; ++sp) {
       const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
       out[sp * total + i] = h;
       x -= (double)__bfloat162float(h);
@@ -524,15 +541,15 @@ __global__ void k_split_bf16(const float* __restrict__ M, const double* __restri
 
 }  // namespace
 
-size_t tc_apre_bytes(int p, bool wide) {
+size_t tc_apre_bytes(int p, int nsplit) {
   const int p3 = p * p * p;
   const int kp = ((p3 + kKC - 1) / kKC) * kKC, nch = kp / kKC, mt = (4 * p3 + 127) / 128;
-  return (size_t)kOffSlots * mt * nch * (wide ? 3 : 2) * kTileBytes;
+  return (size_t)kOffSlots * mt * nch * nsplit * kTileBytes;
 }
 
-size_t tc_bsplit_bytes(int p, int level, bool wide) {
+size_t tc_bsplit_bytes(int p, int level, int nsplit) {
   const size_t W = (size_t)(1 << (level - 1)) + 2 * kHalo;
-  return (wide ? 3 : 2) * 8 * W * W * W * (size_t)tc_padded_k(p) * sizeof(__nv_bfloat16);
+  return (size_t)nsplit * 8 * W * W * W * (size_t)tc_padded_k(p) * sizeof(__nv_bfloat16);
 }
 
 // The 5-D tensor map of a level's split multipoles: dims (KP, W, W, W,
@@ -552,7 +569,7 @@ int make_tc_map(Plan& P, int level) {
   if (!P.tmapB[level]) return FMM_ERR_ALLOC;
   const cuuint64_t kp = (cuuint64_t)tc_padded_k(P.p), W = (cuuint64_t)(1 << (level - 1)) + 2 * kHalo;
   const bool wide = tc_wide(P, level);
-  const cuuint64_t dims[5] = {kp, W, W, W, (cuuint64_t)(wide ? 24 : 16)};
+  const cuuint64_t dims[5] = {kp, W, W, W, (cuuint64_t)(8 * tc_splits(P, level))};
   const cuuint64_t strides[4] = {kp * 2, kp * 2 * W, kp * 2 * W * W, kp * 2 * W * W * W};
   const cuuint32_t box[5] = {(cuuint32_t)kKC, (cuuint32_t)kBX, (cuuint32_t)(wide ? TcMode<6>::BY : TcMode<3>::BY),
                              (cuuint32_t)kBZ, 1};
@@ -597,8 +614,8 @@ cudaError_t setup_m2l_tc(const Plan& P) {
 
 cudaError_t launch_split_bf16(Plan& P, int level, cudaStream_t s) {
   const int p3 = P.p * P.p * P.p;
-  k_split_bf16<<<8 * P.num_sms, 256, 0, s>>>(P.M[level], tc_wide(P, level) ? P.M64[level] : nullptr, p3,
-                                            tc_padded_k(P.p), level, P.iso,
+  k_split_bf16<<<8 * P.num_sms, 256, 0, s>>>(P.M[level], tc_wide(P, level) ? P.M64[level] : nullptr,
+                                            tc_splits(P, level), p3, tc_padded_k(P.p), level, P.iso,
                                             static_cast<__nv_bfloat16*>(P.Mbf_hi[level]));
   return cudaGetLastError();
 }
