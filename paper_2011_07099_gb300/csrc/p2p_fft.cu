@@ -18,14 +18,15 @@
 //
 // Kernels (all spectra are real-input half spectra, kx in [0, M/2]):
 //   k_nz_kernel  plan time: the 27 x 4 kernel spectra, in FP64, rounded once
-//   k_nz_fwd     per leaf: the spectrum of its zero-padded masses
-//   k_nz_mac     per (tile of 4^3 target leaves, chunk of 32 frequencies): the
-//                27-term sums for 4 fields, written per target leaf
-//   k_nz_inv     per target leaf: 4 inverse transforms, only the S^3 cells kept,
-//                plus the L2P far field; writes the final potential and
-//                acceleration.
-// Transforms are direct DFTs along each axis (8 nonzero inputs forward, 8
-// kept outputs inverse), with twiddles from sincospi in FP64.
+//   k_nz_fwd     per leaf: the spectrum of its zero-padded masses (direct
+//                line DFTs of the 8 nonzero inputs per axis)
+//   k_nz_mac     per (tile of 4^3 target leaves, 8 chunks of 32 frequencies):
+//                the 27-term sums for 4 fields, written per target leaf
+//   k_nz_l2p     per leaf: the L2P far field, written to the outputs
+//   k_nz_inv     persistent over the target leaves: 4 inverse transforms
+//                (radix-2 in registers, only the S^3 cells kept) added to the
+//                far field in the outputs.
+// Twiddles come from sincospi in FP64.
 #include "fmm_internal.cuh"
 #include "tc_ptx.cuh"
 
