@@ -35,11 +35,16 @@
 namespace fmm {
 namespace {
 
-template <int P>
+// NT targets per CTA (register budget: NT x 4 fields x (sum, compensation,
+// plane, row) accumulators per thread).  The level-3 split-table kernel
+// (EXT 1) takes 4, so that two CTAs share an SM: with 8 its 169 registers
+// left one 7-warp CTA per SM, waiting on the table-window loads.
+template <int P, int EXT = 0>
 struct M2LShape {
   static constexpr int P3 = P * P * P;
   static constexpr int THREADS = ((P3 + 31) / 32) * 32 < 64 ? 64 : ((P3 + 31) / 32) * 32;
-  static constexpr int NT = P3 > 256 ? 4 : 8;            // targets per CTA (register budget)
+  static constexpr int NT = (P3 > 256 || EXT == 1) ? 4 : 8;
+  static constexpr int PER_SM = EXT == 1 ? 2 : 1;        // CTAs per SM the launch bounds ask for
 };
 
 // EXT: 0 = FP32 table; 1 = the potential also takes G_lo; 2 = all four fields
@@ -47,12 +52,12 @@ struct M2LShape {
 // FP64 copy as hi + lo (the wide levels of high orders, whose masses are
 // large alternating sums).
 template <int P, int EXT>
-__global__ void __launch_bounds__(M2LShape<P>::THREADS)
+__global__ void __launch_bounds__(M2LShape<P, EXT>::THREADS, M2LShape<P, EXT>::PER_SM)
 k_m2l_fp32(const float* __restrict__ M, float* __restrict__ F, const float4* __restrict__ tab,
            const float4* __restrict__ tab_lo, const int8_t* __restrict__ offs, int n_off, int level,
            int per_split, size_t split_stride, int pairs, const double* __restrict__ M64, int iso) {
   constexpr int P3 = P * P * P;
-  constexpr int NT = M2LShape<P>::NT;
+  constexpr int NT = M2LShape<P, EXT>::NT;
   constexpr int D = 2 * P - 1;          // table window per dimension
   constexpr int D3 = D * D * D;
   constexpr int HW = 4 * P - 1, E = 8 * P - 1;
@@ -383,11 +388,14 @@ template <int P>
 cudaError_t launch_p(Plan& Pl, int level, cudaStream_t s) {
   constexpr int P3 = P * P * P;
   constexpr int D = 2 * P - 1;
-  constexpr int NT = M2LShape<P>::NT;
   constexpr int EXT_TOP = P >= 7 ? 2 : 1;
   const int threads = M2LShape<P>::THREADS;
   const bool ext = level <= kExtTopLevel;          // split table
   const bool wide = wide_level(Pl, level);         // (sum, low part) outputs reduced in FP64
+  const double* m64 = wide ? Pl.M64[level] : nullptr;   // FP64 masses: wide levels of the high orders
+  const bool df = level == 2 || m64 || Pl.S >= kWideLeaf;
+  // targets per CTA of the kernel that runs (m2l_fp32_pick)
+  const int NT = (!df && ext) ? M2LShape<P, EXT_TOP>::NT : M2LShape<P>::NT;
   const size_t lo_bytes = ext ? (EXT_TOP == 2 ? sizeof(float4) : sizeof(float)) * D * D * D : 0;
   const size_t smem = sizeof(float4) * (D * D * D + P3 * (NT / 4)) + lo_bytes;
   const uint32_t n_par = 1u << (3 * (level - 1));
@@ -398,11 +406,10 @@ cudaError_t launch_p(Plan& Pl, int level, cudaStream_t s) {
   // wide levels write (sum, low part) pairs per offset range, reduced in FP64
   float* out = wide ? Pl.m2l_part : Pl.F[level];
   dim3 grid((n_par + NT - 1) / NT, 8, nsplit);
-  const double* m64 = wide ? Pl.M64[level] : nullptr;   // FP64 masses: wide levels of the high orders
   // double-float sums: level 2, every wide level of the high orders, and
   // every level with 16-cell leaves (whose L2P amplifies the rounding of the
   // sums that varies from one gridlet point to the next)
-  if (level == 2 || m64 || Pl.S >= kWideLeaf)
+  if (df)
     k_m2l_df<P><<<grid, threads, sizeof(float4) * (2 * D * D * D + 2 * P3 * (NT / 4)), s>>>(
         Pl.M[level], out, Pl.tab[level], Pl.tab_lo[level], Pl.offsets[level], n_off, level, per, field, 1, m64,
         Pl.iso);
@@ -451,9 +458,13 @@ cudaError_t setup_p() {
 
 int m2l_fp32_splits(const Plan& P, int level) {
   if (level > kExtTopLevel) return 1;     // fine levels have targets enough
-  const int nt = P.p * P.p * P.p > 256 ? 4 : 8;
+  // the level-3 split-table kernel of orders < 7: 4 targets per CTA, two
+  // CTAs per SM (M2LShape); the others 8 (4 above 256 gridlet points), one
+  const bool df = level == 2 || (P.p >= kWideOrder && wide_level(P, level)) || P.S >= kWideLeaf;
+  const bool ext1 = !df && P.p < kWideOrder;
+  const int nt = (P.p * P.p * P.p > 256 || ext1) ? 4 : 8;
   const long ctas = (long)(((1u << (3 * (level - 1))) + nt - 1) / nt) * 8;
-  const long sms = P.num_sms > 0 ? P.num_sms : 1;
+  const long sms = (P.num_sms > 0 ? P.num_sms : 1) * (ext1 ? 2 : 1);
   // at least ~4 waves of one CTA per SM, and the range count whose last wave
   // is fullest (these CTAs hold one SM each: registers)
   long lo = (4 * sms + ctas - 1) / ctas, hi = 3 * lo;
