@@ -132,6 +132,11 @@ struct Plan {
   int* d_err = nullptr;                    // device error word (bounded waits that gave up)
   int n_off[kMaxLevel + 1] = {};
 
+  // untimed solves of the tensor-core forms overlap independent stages on
+  // two plan-owned streams (aux), joined by events (fev)
+  cudaStream_t aux[2] = {};
+  cudaEvent_t fev[4] = {};
+
   // per-stage timing: ev[2*k] / ev[2*k+1] bracket slot k
   int timing = 0;
   int timed = 0;
@@ -196,7 +201,9 @@ int prepare_fft(Plan& P);
 cudaError_t launch_m2l_fft(Plan& P, int level, cudaStream_t s);
 void free_fft(Plan& P);
 cudaError_t launch_l2l(Plan& P, int level, cudaStream_t s);       // F[level] -> F[level+1] (adds)
-cudaError_t launch_p2p(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s);
+// near_fwd_done: the FFT near zone's source spectra were already taken (launch_near_fft_fwd).
+cudaError_t launch_p2p(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s,
+                       bool near_fwd_done = false);
 // The near zone by FFT (p2p_fft.cu): whether the plan's shape allows it, the
 // float2 counts of its kernel, source and target spectra, function attributes, the plan-time kernel spectra (after every
 // re-tabulation) and the leaf stage itself (launch_p2p dispatches to it).
@@ -204,7 +211,8 @@ bool near_fft_supported(const Plan& P);
 void near_fft_counts(const Plan& P, size_t& nK, size_t& nM, size_t& nP);
 cudaError_t setup_near_fft(const Plan& P);
 cudaError_t launch_near_fft_kernels(Plan& P, cudaStream_t s);
-cudaError_t launch_near_fft(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s);
+cudaError_t launch_near_fft_fwd(Plan& P, const float* rho, cudaStream_t s);
+cudaError_t launch_near_fft(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s, bool fwd_done);
 cudaError_t setup_m2l_tc(const Plan& P);
 cudaError_t setup_learn();
 cudaError_t launch_residual(const float* phi, const float* acc, const float* tphi, const float* tacc, size_t n3,

@@ -494,8 +494,8 @@ cudaError_t setup_p2p(const Plan& P) {
   }
 }
 
-cudaError_t launch_p2p(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s) {
-  if (P.near_fft) return launch_near_fft(P, rho, phi, acc, s);
+cudaError_t launch_p2p(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s, bool near_fwd_done) {
+  if (P.near_fft) return launch_near_fft(P, rho, phi, acc, s, near_fwd_done);
   switch (P.S) {
     case 1: return launch_s<1>(P, rho, phi, acc, s);
     case 2: return launch_s<2>(P, rho, phi, acc, s);

@@ -1,5 +1,5 @@
 // Leaf stage by fast Fourier transforms: the near zone (P2P) as a sum of
-// zero-padded convolutions, the leaf's L2P fused into the inverse transform.
+// zero-padded convolutions, added to the leaf's L2P far field.
 //
 // Sec. 3 computes the near zone of a regular grid with an FFT under
 // non-periodic boundary conditions, obtained by doubling the grid.  Here that
@@ -609,10 +609,15 @@ cudaError_t launch_near_fft_kernels(Plan& P, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_near_fft(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s) {
+cudaError_t launch_near_fft_fwd(Plan& P, const float* rho, cudaStream_t s) {
+  k_nz_fwd<<<1u << (3 * P.L), kFwdThr, 0, s>>>(rho, P.d_mean, P.N, P.L, P.nz_M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_near_fft(Plan& P, const float* rho, float* phi, float* acc, cudaStream_t s, bool fwd_done) {
   const unsigned nl3 = 1u << (3 * P.L);
   const int nt = (1 << P.L) / kNT;
-  k_nz_fwd<<<nl3, kFwdThr, 0, s>>>(rho, P.d_mean, P.N, P.L, P.nz_M);
+  if (!fwd_done) k_nz_fwd<<<nl3, kFwdThr, 0, s>>>(rho, P.d_mean, P.N, P.L, P.nz_M);
   k_nz_mac<<<dim3(nt * nt * nt, kNCH / kCPC), kMacThr, sizeof(float2) * (128 + 2 * kMacStage), s>>>(
       P.nz_K, P.nz_M, P.nz_P, P.L, P.iso);
   launch_l2p(P, phi, acc, s);
