@@ -184,8 +184,9 @@ int fmm_plan_set_m2l_algorithm(fmm_plan* plan, int algorithm);
  * non-periodic boundary conditions on a doubled grid, the approach Sec. 3
  * takes for the near zone of a regular grid: per pair of neighbour leaves
  * the 8^3 masses zero-padded to 16^3, the 27 x 4 kernel spectra of the near
- * table (FP64, rounded once), FP32 transforms and products; the leaf's L2P is
- * fused into the inverse transform.  Needs 8-cell leaves (N = 8 * 2^L);
+ * table (FP64, rounded once), FP32 transforms and products; the inverse
+ * transforms add the near field to the leaf's L2P far field.  Needs 8-cell
+ * leaves (N = 8 * 2^L);
  * FMM_ERR_UNSUPPORTED otherwise.  Allocates the spectra (synchronous;
  * 2^(3L) x 92 KB: 3.0 GB at 256^3, L = 5) and computes the kernel spectra,
  * again after every re-tabulation.  FMM_NEAR_DIRECT frees them.  FMM_ERR_ARG
