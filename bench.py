@@ -454,6 +454,8 @@ def run_ours(args):
     near_fft = near_fft_used(args)
     if near_fft:
         B.fmm_plan_set_near_algorithm(plan.handle, B.FMM_NEAR_FFT)
+    # the tensor-core tile of each level, autotuned at plan time (outside the timed region)
+    tc_tiles = B.fmm_plan_autotune_tiles(plan.handle, rho)[:L + 1] if tc else None
     with ClockSampler(dev.index) as clk:
         step_ms, stage, wall = _time_solves(B, plan, rho, phi, acc, args.steps, args.warmup, l2_flush, stream,
                                             barrier)
@@ -604,7 +606,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if not tc else ("bf16x3" if prec == B.FMM_PREC_BF16X3 else "bf16"),
         "data": "synthetic",
-        "config": headline_config(args, learned, ws),
+        "config": dict(headline_config(args, learned, ws), tc_tiles=tc_tiles),
         "stage_ms": stage_ms,
         "stage_ms_source": "two solves with the library's stage timing on, which runs the stages one after another; "
                            "the timed steps overlap the CUDA-core M2L levels and the near zone's forward transform "

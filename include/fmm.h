@@ -232,6 +232,23 @@ int fmm_plan_set_m2l_group(fmm_plan* plan, int offsets_per_partial);
  * (synchronously).  FMM_ERR_ARG outside 4..9. */
 int fmm_plan_set_tc_min_level(fmm_plan* plan, int level);
 
+/* Tensor-core tile of one level: targets per CTA, 256 (default: an
+ * 8 x 8 x 4 box of parents, MMA N = 256) or 128 (8 x 4 x 4, N = 128: twice
+ * the CTAs, for levels whose 256-target grid leaves SMs idle).  The results
+ * do not depend on it (each target's sums run in the same order).  The bf16x6
+ * levels always take 128.  level in 4..L; FMM_ERR_ARG otherwise. */
+int fmm_plan_set_tc_tile(fmm_plan* plan, int level, int targets);
+
+/* Autotune the tensor-core tile of every level of the plan's mixed form:
+ * times each tensor-core level's M2L with both tiles (stage-timed solves of
+ * `density`, one warm-up and the faster of two, enqueued on `stream`; the
+ * plan's precision must already be set), keeps the faster per level, and
+ * writes the chosen targets per CTA to tiles[l] for l < n (0 for levels not
+ * on the tensor cores; n may be 0).  Allocates scratch outputs for its
+ * solves (4 N^3 floats) and synchronises.  FMM_ERR_ARG for NULL or
+ * misaligned pointers, FMM_ERR_ALLOC, FMM_ERR_CUDA. */
+int fmm_plan_autotune_tiles(fmm_plan* plan, const float* density, int* tiles, int n, void* stream);
+
 /* Synchronise the device and read the plan's device error word: FMM_OK, or
  * FMM_ERR_TIMEOUT if a bounded device-side wait of an earlier solve gave up
  * (the word is then cleared).  Solves never block forever. */

@@ -75,6 +75,8 @@ SIGNATURES = {
     "fmm_plan_set_green_mesh": (_I, [_VP, _FP, _SZ]),
     "fmm_plan_set_m2l_algorithm": (_I, [_VP, _I]),
     "fmm_plan_set_near_algorithm": (_I, [_VP, _I]),
+    "fmm_plan_set_tc_tile": (_I, [_VP, _I, _I]),
+    "fmm_plan_autotune_tiles": (_I, [_VP, _VP, ctypes.POINTER(ctypes.c_int), _I, _VP]),
     "fmm_batch_set_near_algorithm": (_I, [_VP, _I]),
     "fmm_plan_set_table_grid": (_I, [_VP, _FP, _SZ]),
     "fmm_table_grid_grad": (_I, [_VP, _FP, _FP, _FP, ctypes.c_float, ctypes.c_float, _FP, _FP, _VP]),
@@ -243,6 +245,20 @@ def fmm_plan_set_m2l_algorithm(plan, algorithm):
 
 def fmm_plan_set_near_algorithm(plan, algorithm):
     _check(lib().fmm_plan_set_near_algorithm(plan, int(algorithm)), "fmm_plan_set_near_algorithm")
+
+
+def fmm_plan_set_tc_tile(plan, level, targets):
+    _check(lib().fmm_plan_set_tc_tile(plan, int(level), int(targets)), "fmm_plan_set_tc_tile")
+
+
+def fmm_plan_autotune_tiles(plan, density, stream=None):
+    """Tuned tensor-core tiles: a list, targets per CTA per level (0 where a
+    level is not on the tensor cores)."""
+    n = 9                                   # levels 0..8, the deepest tree the library builds
+    out = (ctypes.c_int * n)()
+    _check(lib().fmm_plan_autotune_tiles(plan, density.data_ptr(), out, n, _stream_of(density, stream)),
+           "fmm_plan_autotune_tiles")
+    return list(out)
 
 
 def fmm_batch_set_near_algorithm(batch, algorithm):

@@ -552,6 +552,61 @@ int fmm_plan_set_tc_min_level(fmm_plan* plan, int level) {
   return set_err(FMM_OK);
 }
 
+int fmm_plan_set_tc_tile(fmm_plan* plan, int level, int targets) {
+  if (!plan || (targets != 128 && targets != 256)) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  if (level < fmm::kTcMinLevel || level > P.L) return set_err(FMM_ERR_ARG);
+  P.tc_tile[level] = targets == 128 ? 128 : 0;
+  if (P.tmapB[level]) {     // the tensor loads' box follows the tile
+    FMM_CUDA_TRY(cudaDeviceSynchronize());
+    const int rc = fmm::make_tc_map(P, level);
+    if (rc != FMM_OK) return set_err(rc);
+  }
+  return set_err(FMM_OK);
+}
+
+int fmm_plan_autotune_tiles(fmm_plan* plan, const float* density, int* tiles, int n, void* stream) {
+  if (!plan || !density || !aligned16(density) || (n > 0 && !tiles) || n < 0) return set_err(FMM_ERR_ARG);
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  const bool tc = P.prec != FMM_PREC_FP32 && P.tc_ready;
+  const size_t n3 = (size_t)P.N * P.N * P.N;
+  if (tc) {
+    float* out = nullptr;
+    if (cudaMalloc(&out, sizeof(float) * 4 * n3) != cudaSuccess) return set_err(FMM_ERR_ALLOC);
+    const int was_timing = P.timing;
+    int rc = fmm_plan_set_timing(plan, 1);
+    float best[fmm::kMaxLevel + 1] = {};
+    int pick[fmm::kMaxLevel + 1] = {};
+    for (int c = 0; c < 2 && rc == FMM_OK; ++c) {
+      const int t = c == 0 ? 256 : 128;
+      for (int l = fmm::tc_first_level(P); l <= P.L && rc == FMM_OK; ++l)
+        if (!fmm::tc_wide(P, l)) rc = fmm_plan_set_tc_tile(plan, l, t);
+      float ms[FMM_TIME_SLOTS];
+      float lev[fmm::kMaxLevel + 1];
+      for (int l = 0; l <= fmm::kMaxLevel; ++l) lev[l] = 1e30f;
+      for (int r = 0; r < 3 && rc == FMM_OK; ++r) {      // one warm-up, then the faster of two
+        rc = fmm_solve(plan, density, out, out + n3, stream);
+        if (rc == FMM_OK) rc = fmm_plan_stage_times(plan, ms, FMM_TIME_SLOTS);
+        for (int l = 2; l <= P.L && r > 0 && rc == FMM_OK; ++l)
+          lev[l] = ms[FMM_TIME_M2L_LEVEL0 + l] < lev[l] ? ms[FMM_TIME_M2L_LEVEL0 + l] : lev[l];
+      }
+      for (int l = 2; l <= P.L && rc == FMM_OK; ++l)
+        if (c == 0 || lev[l] < best[l]) {
+          best[l] = lev[l];
+          pick[l] = t;
+        }
+    }
+    for (int l = fmm::tc_first_level(P); l <= P.L && rc == FMM_OK; ++l)
+      if (!fmm::tc_wide(P, l)) rc = fmm_plan_set_tc_tile(plan, l, pick[l]);
+    fmm_plan_set_timing(plan, was_timing);
+    cudaFree(out);
+    if (rc != FMM_OK) return set_err(rc);
+  }
+  for (int l = 0; l < n; ++l)
+    tiles[l] = (tc && l <= P.L && l >= fmm::tc_first_level(P)) ? fmm::tc_targets(P, l) : 0;
+  return set_err(FMM_OK);
+}
+
 int fmm_plan_set_correction_inference(fmm_plan* plan, int mode) {
   if (!plan || (mode != FMM_INFER_BF16 && mode != FMM_INFER_FP32)) return set_err(FMM_ERR_ARG);
   reinterpret_cast<Plan*>(plan)->corr_fp32 = mode == FMM_INFER_FP32 ? 1 : 0;

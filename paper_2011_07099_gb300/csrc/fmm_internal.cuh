@@ -102,6 +102,7 @@ struct Plan {
   void* Mbf_lo[kMaxLevel + 1] = {};        // unused (kept null)
   void* Apre[kMaxLevel + 1] = {};          // precomputed split translation tiles per offset slot
   int tc_group = 4;                        // offsets accumulated per TMEM partial before promotion
+  int tc_tile[kMaxLevel + 1] = {};         // targets per tensor-core CTA per level: 0 (= 256) or 128
   int m2l_fft = 0;                         // FFT form of the interaction zone at the fine levels (ablation)
   void* fft = nullptr;                     // its cuFFT plans and buffers (m2l_fft.cu)
   int tc_min_level = kTcMinLevel;          // first level on the tensor cores in the mixed forms
@@ -247,6 +248,9 @@ int tc_padded_k(int p);
 // into a double-float total.
 inline bool tc_wide(const Plan& P, int l) { return wide_level(P, l); }
 inline int tc_splits(const Plan& P, int l) { return tc_wide(P, l) ? 3 : 2; }
+// Targets per tensor-core CTA at level l: 128 in the wide mode, else the
+// plan's tile (fmm_plan_set_tc_tile), 256 by default.
+inline int tc_targets(const Plan& P, int l) { return tc_wide(P, l) || P.tc_tile[l] == 128 ? 128 : 256; }
 size_t tc_apre_bytes(int p, int nsplit);
 size_t tc_bsplit_bytes(int p, int level, int nsplit);
 // Encodes P.tmapB[level] for P.Mbf_hi[level] (FMM_* code).

@@ -80,12 +80,17 @@ constexpr int kTileBytes = 128 * kKC * 2;     // one 128 x 32 BF16 tile of A
 // parts and ten products measured the same error at order 8, level 4: there
 // the truncating accumulation inside each stage's MMAs, not the operands,
 // limits; that level stays on the double-float CUDA-core kernel.)
-template <int MODE>
+// NTT: targets per CTA (MMA N), 256 or 128 (an 8 x 8 x 4 or 8 x 4 x 4 box of
+// parents); the wide mode always takes 128 (TMEM room for the double-float
+// total), the others 256 unless the plan's tile for the level says 128.
+template <int MODE, int NTT = (MODE >= 6 ? 128 : 256)>
 struct TcMode {
   static constexpr bool WIDE = MODE >= 6;
   static constexpr int NSPLIT = MODE == 6 ? 3 : (MODE == 3 ? 2 : 1);   // splits of each operand used
   static constexpr int ASPLIT = WIDE ? NSPLIT : 2;                     // A tiles stored per stage
-  static constexpr int NT = WIDE ? 128 : 256;                          // targets per CTA (MMA N)
+  static constexpr int NT = NTT;                                       // targets per CTA (MMA N)
+  static_assert(NT == 128 || NT == 256, "target tile");
+  static_assert(!WIDE || NT == 128, "the wide mode's TMEM layout needs 128 targets");
   static constexpr int BY = NT / (kBX * kBZ);
   static constexpr int TILEB = NT * kKC * 2;                           // one NT x 32 BF16 tile of B
   // drain threads: bf16x6 adds a partial per stage into a double-float total,
@@ -94,14 +99,14 @@ struct TcMode {
   static constexpr int THREADS = 64 + DRAIN;
 };
 
-template <int P, int MODE>
+template <int P, int MODE, int NTT = TcMode<MODE>::NT>
 struct TcShape {
   static constexpr int P3 = P * P * P;
   static constexpr int KP = ((P3 + kKC - 1) / kKC) * kKC;   // padded reduction length per offset
   static constexpr int NCH = KP / kKC;                       // stages per offset
   static constexpr int MT = (4 * P3 + 127) / 128;            // row tiles
-  static constexpr int NSPLIT = TcMode<MODE>::NSPLIT;
-  static constexpr int STAGE_BYTES = NSPLIT * (kTileBytes + TcMode<MODE>::TILEB);
+  static constexpr int NSPLIT = TcMode<MODE, NTT>::NSPLIT;
+  static constexpr int STAGE_BYTES = NSPLIT * (kTileBytes + TcMode<MODE, NTT>::TILEB);
   static constexpr int EXTRA = 64;
   static constexpr int LIMIT = 225 * 1024;                  // dynamic shared memory budget
   static constexpr int FIT = (LIMIT - EXTRA - 1024) / STAGE_BYTES;
@@ -114,13 +119,13 @@ struct TcShape {
 __host__ __device__ constexpr int off_index(int ox, int oy, int oz) { return ((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3); }
 constexpr int kOffSlots = 343;
 
-template <int P, int MODE>
+template <int P, int MODE, int NTT>
 __global__ void __launch_bounds__(64 + kDrainMax, 1)
 k_m2l_tc(const __grid_constant__ CUtensorMap tmapB, const uint8_t* __restrict__ Apre,
          const int8_t* __restrict__ offs, int n_off, int level, int group,
          float* __restrict__ F, double* __restrict__ F64, int* __restrict__ err, uint64_t kWaitNs, int stall) {
-  using Sh = TcShape<P, MODE>;
-  using Md = TcMode<MODE>;
+  using Sh = TcShape<P, MODE, NTT>;
+  using Md = TcMode<MODE, NTT>;
   constexpr int P3 = Sh::P3, NCH = Sh::NCH, MT = Sh::MT, ST = Sh::ST, NSPLIT = Sh::NSPLIT;
   constexpr int STAGE_BYTES = Sh::STAGE_BYTES;
   constexpr int kNT = Md::NT, kBY = Md::BY, kTileB = Md::TILEB, ASPLIT = Md::ASPLIT;
@@ -402,26 +407,26 @@ __global__ void k_build_a(const uint4* __restrict__ tabbf, uint8_t* __restrict__
   }
 }
 
-template <int P, int MODE>
+template <int P, int MODE, int NTT>
 constexpr size_t smem_bytes() {
-  return (size_t)TcShape<P, MODE>::SMEM;
+  return (size_t)TcShape<P, MODE, NTT>::SMEM;
 }
 
-template <int P, int MODE>
+template <int P, int MODE, int NTT = TcMode<MODE>::NT>
 cudaError_t setup_one() {
-  return cudaFuncSetAttribute(k_m2l_tc<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_bytes<P, MODE>());
+  return cudaFuncSetAttribute(k_m2l_tc<P, MODE, NTT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_bytes<P, MODE, NTT>());
 }
 
-template <int P, int MODE>
+template <int P, int MODE, int NTT = TcMode<MODE>::NT>
 cudaError_t launch_one(Plan& Pl, int level, cudaStream_t s) {
   const int nh = 1 << (level - 1);
   // target boxes fastest: the CTAs in flight share row tile and child type,
   // hence their A tiles, which L2 then serves to all of them
-  dim3 grid((nh / kBX) * (nh / TcMode<MODE>::BY) * (nh / kBZ), TcShape<P, MODE>::MT, 8);
+  dim3 grid((nh / kBX) * (nh / TcMode<MODE, NTT>::BY) * (nh / kBZ), TcShape<P, MODE, NTT>::MT, 8);
   const CUtensorMap* map = static_cast<const CUtensorMap*>(Pl.tmapB[level]);
   const uint8_t* Apre = static_cast<const uint8_t*>(Pl.Apre[level]);
-  k_m2l_tc<P, MODE><<<grid, TcMode<MODE>::THREADS, smem_bytes<P, MODE>(), s>>>(
+  k_m2l_tc<P, MODE, NTT><<<grid, TcMode<MODE, NTT>::THREADS, smem_bytes<P, MODE, NTT>(), s>>>(
       *map, Apre, Pl.offsets[level], Pl.n_off[level], level, Pl.tc_group, Pl.F[level], Pl.F64[level], Pl.d_err,
       Pl.wait_ns, Pl.inject_stall);
   return cudaGetLastError();
@@ -431,6 +436,8 @@ template <int P>
 cudaError_t setup_p() {
   cudaError_t e;
   if ((e = setup_one<P, 1>()) != cudaSuccess) return e;
+  if ((e = setup_one<P, 1, 128>()) != cudaSuccess) return e;
+  if ((e = setup_one<P, 3, 128>()) != cudaSuccess) return e;
   constexpr int PW = P >= kWideOrder ? P : kWideOrder;   // the wide modes exist at high orders only
   if (P >= kWideOrder && (e = setup_one<PW, 6>()) != cudaSuccess) return e;
   return setup_one<P, 3>();
@@ -443,8 +450,9 @@ cudaError_t launch_p(Plan& Pl, int level, int mode, cudaStream_t s) {
     if (P < kWideOrder) return cudaErrorInvalidValue;
     return launch_one<PW, 6>(Pl, level, s);
   }
-  if (mode == FMM_PREC_BF16X3) return launch_one<P, 3>(Pl, level, s);
-  return launch_one<P, 1>(Pl, level, s);
+  const bool t128 = tc_targets(Pl, level) == 128;
+  if (mode == FMM_PREC_BF16X3) return t128 ? launch_one<P, 3, 128>(Pl, level, s) : launch_one<P, 3>(Pl, level, s);
+  return t128 ? launch_one<P, 1, 128>(Pl, level, s) : launch_one<P, 1>(Pl, level, s);
 }
 
 // Plan time, wide levels: the translation tiles split in NS BF16 parts from
@@ -568,10 +576,9 @@ int make_tc_map(Plan& P, int level) {
   if (!P.tmapB[level]) P.tmapB[level] = new (std::nothrow) CUtensorMap;
   if (!P.tmapB[level]) return FMM_ERR_ALLOC;
   const cuuint64_t kp = (cuuint64_t)tc_padded_k(P.p), W = (cuuint64_t)(1 << (level - 1)) + 2 * kHalo;
-  const bool wide = tc_wide(P, level);
   const cuuint64_t dims[5] = {kp, W, W, W, (cuuint64_t)(8 * tc_splits(P, level))};
   const cuuint64_t strides[4] = {kp * 2, kp * 2 * W, kp * 2 * W * W, kp * 2 * W * W * W};
-  const cuuint32_t box[5] = {(cuuint32_t)kKC, (cuuint32_t)kBX, (cuuint32_t)(wide ? TcMode<6>::BY : TcMode<3>::BY),
+  const cuuint32_t box[5] = {(cuuint32_t)kKC, (cuuint32_t)kBX, (cuuint32_t)(tc_targets(P, level) / (kBX * kBZ)),
                              (cuuint32_t)kBZ, 1};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   const CUresult r = encode(static_cast<CUtensorMap*>(P.tmapB[level]), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5,

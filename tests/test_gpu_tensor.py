@@ -143,3 +143,39 @@ def test_bounded_wait_expires_and_context_survives(B, limit_ms):
         assert_close(phi.cpu().numpy(), ophi, TOL_BF16X3, "after timeout phi")
         assert_close(acc.cpu().numpy(), og, TOL_BF16X3, "after timeout g")
     plan.close()
+
+
+def test_tile_of_128_targets_equals_256_bitwise(B):
+    # the 128-target tile (8 x 4 x 4 parents per CTA) runs every target's
+    # sums in the same order as the 256-target one: results equal bit for bit
+    N, L, p = 128, 5, 4                    # tensor-core levels 4 and 5
+    rho = torch.from_numpy(inputs.lognormal(N, sigma=0.5, seed=11)).cuda()
+    out = []
+    for tile in (256, 128):
+        plan = B.Plan(N, L, p)
+        plan.set_precision(B.FMM_PREC_BF16X3)
+        for lev in (4, 5):
+            B.fmm_plan_set_tc_tile(plan.handle, lev, tile)
+        phi, acc = plan.solve(rho)
+        torch.cuda.synchronize()
+        assert B.lib().fmm_plan_check(plan.handle) == B.FMM_OK
+        out.append((phi, acc))
+        plan.close()
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+
+
+def test_tile_autotuner_picks_valid_tiles_and_keeps_the_results(B):
+    N, L, p = 128, 5, 4
+    rho = torch.from_numpy(inputs.lognormal(N, sigma=0.5, seed=12)).cuda()
+    plan = B.Plan(N, L, p)
+    plan.set_precision(B.FMM_PREC_BF16X3)
+    phi0, acc0 = plan.solve(rho)
+    torch.cuda.synchronize()
+    tiles = B.fmm_plan_autotune_tiles(plan.handle, rho)
+    print("tuned tiles per level:", tiles[:L + 1])
+    assert tiles[2] == 0 and tiles[3] == 0 and tiles[4] in (128, 256) and tiles[5] in (128, 256)
+    phi1, acc1 = plan.solve(rho)
+    torch.cuda.synchronize()
+    assert B.lib().fmm_plan_check(plan.handle) == B.FMM_OK
+    assert torch.equal(phi0, phi1) and torch.equal(acc0, acc1)
+    plan.close()
