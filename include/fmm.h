@@ -464,8 +464,8 @@ int fmm_table_grid_grad(fmm_plan* plan, const float* density, const float* targe
  * independent chains of iters x 16 dependent FMAs, and stores one float per
  * CTA to `out` (device, `blocks` floats).  fmm_probe_fma_flops(blocks, iters)
  * returns the flops one launch performs (2 per FMA), so a caller that times
- * the launch with CUDA events measures the FP32 CUDA-core peak against which
- * the near-zone sum (an FMA-bound step) is judged.  FMM_ERR_ARG for a NULL
+ * the launch with CUDA events measures the FP32 CUDA-core peak, the roofline
+ * of the FMA-bound steps (the near-zone sum, CUDA-core M2L).  FMM_ERR_ARG for a NULL
  * pointer or counts < 1. */
 int fmm_probe_fma(float* out, int blocks, int iters, void* stream);
 double fmm_probe_fma_flops(int blocks, int iters);

@@ -1,5 +1,5 @@
 // Measurement aid: a kernel that does nothing but dependent-chain FP32 FMAs,
-// so that the FP32 CUDA-core peak the near-zone kernel is judged against is
+// so that the FP32 CUDA-core peak, the roofline of the FMA-bound kernels, is
 // measured on the device rather than derived from a nominal clock.
 #include "fmm_internal.cuh"
 
