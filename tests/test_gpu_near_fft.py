@@ -111,3 +111,25 @@ def test_headline_form_with_near_fft_at_sampled_leaves(B):
     got = leaf_values(phi, acc, leaves, N >> L)
     assert_close(got[:, 0], ref[:, 0], TOL_BF16X3, "headline form + near FFT phi, sampled leaves")
     assert_close(got[:, 1:], ref[:, 1:], TOL_BF16X3, "headline form + near FFT g, sampled leaves")
+
+
+def test_overlapped_solve_equals_the_serial_one_bitwise(B):
+    # an untimed solve of the tensor-core form runs the CUDA-core M2L levels
+    # and the near zone's forward transform on the plan's own streams beside
+    # the tensor-core levels; a stage-timed solve runs every stage in turn.
+    # Same kernels on disjoint buffers: the results are equal bit for bit,
+    # also for a second overlapped solve right after (the streams rejoin).
+    N, L, p = 128, 4, 6
+    rho = torch.from_numpy(inputs.lognormal(N, sigma=0.5, seed=21)).cuda()
+    plan = B.Plan(N, L, p)
+    plan.set_precision(B.FMM_PREC_BF16X3)
+    B.fmm_plan_set_near_algorithm(plan.handle, B.FMM_NEAR_FFT)
+    phi0, acc0 = plan.solve(rho)
+    phi1, acc1 = plan.solve(rho)
+    B.fmm_plan_set_timing(plan.handle, 1)
+    phi2, acc2 = plan.solve(rho)
+    torch.cuda.synchronize()
+    assert B.lib().fmm_plan_check(plan.handle) == B.FMM_OK
+    plan.close()
+    for phi, acc in ((phi1, acc1), (phi2, acc2)):
+        assert torch.equal(phi0, phi) and torch.equal(acc0, acc)
