@@ -24,13 +24,14 @@
 // reads: whole lines from L2, no per-lane gathers.
 //
 // CTA tile: 128 rows of (f, r) x 256 targets (one M = 128, N = 256 MMA per
-// 16-deep k step).  Warp roles:
+// 16-deep k step), or x 128 targets per the plan's tile for the level (an
+// 8 x 4 x 4 box of parents; always in bf16x6).  Warp roles:
 //   warp 0      issues the MMAs (one thread);
 //   warp 1      one thread arms each stage's barrier with the stage's bytes
 //               and issues its bulk copies (A) and tensor loads (B);
-//   warps 2..5  drain TMEM: every G offsets accumulate into a fresh TMEM
-//               partial, which the drain warps add into an FP32 total kept in
-//               TMEM while the issuer waits.  A single TMEM accumulator over
+//   warps 2..5  drain TMEM (warps 2..9 in bf16x6): every G offsets
+//               accumulate into a fresh TMEM partial, which the drain warps
+//               add into an FP32 total kept in TMEM while the issuer waits.  A single TMEM accumulator over
 //               all 189 p^3 terms drifts by ~1e-4 on the coherent, cancelling
 //               far-field sums (the accumulation inside the MMA truncates);
 //               per-group partials summed in FP32 with rounding to nearest
