@@ -142,7 +142,6 @@ void free_plan(Plan* P) {
   for (int l = 0; l <= fmm::kMaxLevel; ++l) {
     cudaFree(P->tab_bf[l]);
     cudaFree(P->Mbf_hi[l]);
-    cudaFree(P->Mbf_lo[l]);
     cudaFree(P->Apre[l]);
     delete static_cast<CUtensorMap*>(P->tmapB[l]);
   }

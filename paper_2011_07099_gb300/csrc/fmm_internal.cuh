@@ -96,10 +96,9 @@ struct Plan {
   int8_t* offsets[kMaxLevel + 1] = {};  // per level: [8 child types][n_off][3] (dx, dy, dz) = T - S
   // tensor-core M2L (levels >= kTcMinLevel, allocated on the first mixed-precision solve)
   uint4* tab_bf[kMaxLevel + 1] = {};       // per table entry, per field: bf16 hi | bf16 lo << 16
-  void* Mbf_hi[kMaxLevel + 1] = {};        // gridlet masses split into bf16 hi / lo, per parity class with a halo
+  void* Mbf_hi[kMaxLevel + 1] = {};        // gridlet masses split into BF16 parts (2; 3 at bf16x6 levels), per parity class with a halo
                                            // (layout in m2l_tc.cu, k_split_bf16), rows padded to KP
   void* tmapB[kMaxLevel + 1] = {};         // host CUtensorMap of each Mbf_hi level (the tensor loads of B)
-  void* Mbf_lo[kMaxLevel + 1] = {};        // unused (kept null)
   void* Apre[kMaxLevel + 1] = {};          // precomputed split translation tiles per offset slot
   int tc_group = 4;                        // offsets accumulated per TMEM partial before promotion
   int tc_tile[kMaxLevel + 1] = {};         // targets per tensor-core CTA per level: 0 (= 256) or 128
